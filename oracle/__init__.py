@@ -1,0 +1,112 @@
+"""CPU oracle for windowed median/MAD RFI excision (Section II-D, Eq. 1 and Eq. 2).
+
+TEST INFRASTRUCTURE: only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline leg may import this package. The definition it computes, and every reading it takes
+where the paper is silent, is stated in ``rfi_oracle.cpp``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .build import build
+
+_lock = threading.Lock()
+_lib = None
+
+ZERO, CONST, CLIP, NOISE = 0, 1, 2, 3
+STATUS_OK, STATUS_BAD_ARG, STATUS_SAMPLE_RANGE = 0, 1, 6
+
+
+class OracleArgs(ctypes.Structure):
+    _fields_ = [
+        ("x", ctypes.c_void_p), ("z", ctypes.c_void_p), ("bits", ctypes.c_int32),
+        ("len", ctypes.c_int64), ("W", ctypes.c_int32), ("abs0", ctypes.c_int64),
+        ("n_sigma", ctypes.c_double), ("mode", ctypes.c_int32), ("const_value", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32),
+        ("mask", ctypes.c_void_p), ("counts", ctypes.c_void_p), ("median", ctypes.c_void_p),
+        ("mad", ctypes.c_void_p), ("nthreads", ctypes.c_int32),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.oracle_excise.restype = ctypes.c_int
+            L.oracle_excise.argtypes = [ctypes.POINTER(OracleArgs)]
+            L.oracle_k_q16.restype = ctypes.c_int64
+            L.oracle_k_q16.argtypes = [ctypes.c_double]
+            L.oracle_philox4x32_10.restype = None
+            L.oracle_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
+            L.oracle_noise_value.restype = ctypes.c_int32
+            L.oracle_noise_value.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                             ctypes.c_uint32, ctypes.c_int64, ctypes.c_int32]
+            L.oracle_median_mad.restype = None
+            L.oracle_median_mad.argtypes = [ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32)]
+            _lib = L
+    return _lib
+
+
+def k_q16(k: float) -> int:
+    """k*1.4826 in Q16, rounded half up (the fixed-point form of Eq. 1's multiple)."""
+    return int(lib().oracle_k_q16(float(k)))
+
+
+def philox4x32_10(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().oracle_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def noise_value(M: int, D: int, seed: int, stream_id: int, idx: int, bits: int = 8) -> int:
+    return int(lib().oracle_noise_value(M, D, seed, stream_id, idx, bits))
+
+
+def median_mad(x) -> tuple[int, int]:
+    """Lower median M and lower-median MAD D of one window of integers."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.int32))
+    M, D = ctypes.c_int32(), ctypes.c_int32()
+    lib().oracle_median_mad(a.ctypes.data, a.size, ctypes.byref(M), ctypes.byref(D))
+    return M.value, D.value
+
+
+def mask_words(W: int, n_windows: int) -> int:
+    return n_windows * ((W + 31) // 32)
+
+
+def excise(x: np.ndarray, W: int, k: float, mode: int, const: int = 0, seed: int = 0,
+           stream_id: int = 0, abs0: int = 0, bits: int | None = None, threads: int = 1,
+           out: np.ndarray | None = None, want=("z", "mask", "counts", "median", "mad")):
+    """Excise one stream (or a window-aligned slice of one). Returns a dict of numpy arrays
+    plus ``status`` (0 ok, 1 bad argument, 6 12-bit sample out of range)."""
+    x = np.ascontiguousarray(x)
+    if bits is None:
+        bits = 8 if x.dtype == np.int8 else 12
+    assert x.dtype == (np.int8 if bits == 8 else np.int16)
+    n = x.size
+    nw = -(-n // W) if (n > 0 and W > 0) else 0
+    res = {}
+    z = out if out is not None else np.empty_like(x)
+    res["z"] = z
+    res["mask"] = np.zeros(mask_words(W, nw), np.uint32) if "mask" in want else None
+    res["counts"] = np.zeros(nw, np.uint32) if "counts" in want else None
+    res["median"] = np.zeros(nw, np.int32) if "median" in want else None
+    res["mad"] = np.zeros(nw, np.int32) if "mad" in want else None
+
+    def p(a):
+        return None if a is None else a.ctypes.data
+
+    args = OracleArgs(x.ctypes.data, z.ctypes.data, bits, n, W, abs0, float(k), mode, const,
+                      seed, stream_id, p(res["mask"]), p(res["counts"]), p(res["median"]),
+                      p(res["mad"]), max(1, int(threads)))
+    res["status"] = int(lib().oracle_excise(ctypes.byref(args)))
+    return res
