@@ -1,0 +1,258 @@
+"""ctypes binding of librfi (include/rfi.h): argument marshalling only.
+
+Every function named ``rfi_*`` here calls the C entry point of the same name. Buffers may be
+given as integers (raw pointers), torch tensors (``data_ptr()``) or numpy arrays (host buffers
+for ``rfi_excise_host``). All computation happens in the CUDA kernels of librfi.so; there is no
+fallback: if the library cannot be loaded, importing this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+RFI_OK = 0
+RFI_ERR_INVALID_ARG = 1
+RFI_ERR_UNSUPPORTED = 2
+RFI_ERR_ALIGNMENT = 3
+RFI_ERR_OOM = 4
+RFI_ERR_CUDA = 5
+RFI_ERR_SAMPLE_RANGE = 6
+RFI_ERR_TIMEOUT = 7
+RFI_ERR_BUSY = 8
+
+RFI_REPLACE_ZERO, RFI_REPLACE_CONST, RFI_REPLACE_CLIP, RFI_REPLACE_NOISE = 0, 1, 2, 3
+
+RFI_PLAN_PER_STREAM = 0x1
+RFI_PLAN_BATCHED = 0x2
+RFI_PLAN_GRAPH = 0x4
+RFI_PLAN_AUTOTUNE = 0x8
+RFI_PLAN_INJECT_TIMEOUT = 0x100
+
+
+class RfiLaunchShape(ctypes.Structure):
+    _fields_ = [("consumer_warps", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("stage_bytes", ctypes.c_int32),
+                ("dynamic_tiles", ctypes.c_int32), ("hist_copies", ctypes.c_int32)]
+
+
+class RfiPlanDesc(ctypes.Structure):
+    _fields_ = [("sample_bits", ctypes.c_int32), ("num_streams", ctypes.c_int32),
+                ("stream_len", ctypes.POINTER(ctypes.c_int64)),
+                ("window_len", ctypes.POINTER(ctypes.c_int32)),
+                ("stream_id", ctypes.POINTER(ctypes.c_uint32)), ("k", ctypes.c_double),
+                ("mode", ctypes.c_int32), ("const_value", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32), ("shape", ctypes.POINTER(RfiLaunchShape))]
+
+
+class RfiTotals(ctypes.Structure):
+    _fields_ = [("windows", ctypes.c_uint64), ("flagged", ctypes.c_uint64),
+                ("device_status", ctypes.c_int32)]
+
+
+class RfiPlanInfo(ctypes.Structure):
+    _fields_ = [("k_q16", ctypes.c_int64), ("total_windows", ctypes.c_uint64),
+                ("total_samples", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64),
+                ("tiles", ctypes.c_int32), ("grid", ctypes.c_int32), ("shape", RfiLaunchShape),
+                ("sm_count", ctypes.c_int32), ("kernels_per_call", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+
+def _load():
+    path = _build.LIB
+    if _build.stale():
+        try:
+            path = _build.build()
+        except Exception as e:  # no toolkit and no library: fail loudly
+            if not os.path.exists(_build.LIB):
+                raise ImportError("librfi.so is missing and could not be built: %s" % e) from e
+    lib = ctypes.CDLL(path)
+    sig = {
+        "rfi_plan_create": (ctypes.c_int, [ctypes.POINTER(RfiPlanDesc), ctypes.POINTER(_P)]),
+        "rfi_excise": (ctypes.c_int, [_P, _PP, _PP, _PP, _PP, _P]),
+        "rfi_excise_host": (ctypes.c_int, [_P, _PP, _PP, _PP, _PP, _P]),
+        "rfi_stats": (ctypes.c_int, [_P, _PP, _PP, ctypes.POINTER(RfiTotals), _P]),
+        "rfi_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(RfiPlanInfo)]),
+        "rfi_plan_destroy": (ctypes.c_int, [_P]),
+        "rfi_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "rfi_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB = _load()
+LIB_PATH = _build.LIB
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return int(x.ctypes.data)
+    raise TypeError("cannot take a pointer of %r" % type(x))
+
+
+def _ptr_array(seq):
+    if seq is None:
+        return None
+    arr = (ctypes.c_void_p * len(seq))(*[_ptr(x) or None for x in seq])
+    return ctypes.cast(arr, _PP), arr
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def make_desc(bits, stream_len, window_len, k, mode, const_value=0, seed=0, flags=0, stream_id=None,
+              shape=None):
+    n = len(stream_len)
+    keep = []
+    lens = (ctypes.c_int64 * n)(*[int(v) for v in stream_len])
+    wins = (ctypes.c_int32 * n)(*[int(v) for v in window_len])
+    keep += [lens, wins]
+    sid = None
+    if stream_id is not None:
+        sid = (ctypes.c_uint32 * n)(*[int(v) for v in stream_id])
+        keep.append(sid)
+    shp = None
+    if shape is not None:
+        if not isinstance(shape, RfiLaunchShape):
+            shape = RfiLaunchShape(**shape)
+        shp = ctypes.pointer(shape)
+        keep.append(shape)
+    d = RfiPlanDesc(int(bits), n, lens, wins, sid, float(k), int(mode), int(const_value), int(seed),
+                    int(flags), shp)
+    d._keep = keep
+    return d
+
+
+# ---------------------------------------------------------------- C entry points
+def rfi_plan_create(desc: RfiPlanDesc):
+    h = ctypes.c_void_p()
+    st = LIB.rfi_plan_create(ctypes.byref(desc), ctypes.byref(h))
+    return st, h.value
+
+
+def rfi_excise(plan, ins, outs, masks=None, counts=None, stream=None) -> int:
+    a, b, c, d = _ptr_array(ins), _ptr_array(outs), _ptr_array(masks), _ptr_array(counts)
+    return LIB.rfi_excise(plan, a[0] if a else None, b[0] if b else None, c[0] if c else None,
+                          d[0] if d else None, _stream(stream))
+
+
+def rfi_excise_host(plan, ins, outs, masks=None, counts=None, stream=None) -> int:
+    a, b, c, d = _ptr_array(ins), _ptr_array(outs), _ptr_array(masks), _ptr_array(counts)
+    return LIB.rfi_excise_host(plan, a[0] if a else None, b[0] if b else None, c[0] if c else None,
+                               d[0] if d else None, _stream(stream))
+
+
+def rfi_stats(plan, medians=None, mads=None, stream=None):
+    t = RfiTotals()
+    a, b = _ptr_array(medians), _ptr_array(mads)
+    st = LIB.rfi_stats(plan, a[0] if a else None, b[0] if b else None, ctypes.byref(t), _stream(stream))
+    return st, t
+
+
+def rfi_plan_get_info(plan):
+    info = RfiPlanInfo()
+    st = LIB.rfi_plan_get_info(plan, ctypes.byref(info))
+    return st, info
+
+
+def rfi_plan_destroy(plan) -> int:
+    return LIB.rfi_plan_destroy(plan)
+
+
+def rfi_status_string(status: int) -> str:
+    return LIB.rfi_status_string(int(status)).decode()
+
+
+def rfi_version() -> str:
+    return LIB.rfi_version().decode()
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class RfiError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s: %s (%d)" % (what, rfi_status_string(status), status))
+        self.status = status
+
+
+def check(status: int, what: str):
+    if status != RFI_OK:
+        raise RfiError(status, what)
+
+
+class Plan:
+    """Owns one rfi_plan_t. Buffers are torch tensors (or raw device pointers)."""
+
+    def __init__(self, bits, stream_len, window_len, k, mode, const_value=0, seed=0, flags=0,
+                 stream_id=None, shape=None):
+        self.desc = make_desc(bits, stream_len, window_len, k, mode, const_value, seed, flags,
+                              stream_id, shape)
+        st, h = rfi_plan_create(self.desc)
+        check(st, "rfi_plan_create")
+        self.handle = h
+        self.bits = bits
+        self.stream_len = [int(v) for v in stream_len]
+        self.window_len = [int(v) for v in window_len]
+
+    @property
+    def num_windows(self):
+        return [-(-n // w) for n, w in zip(self.stream_len, self.window_len)]
+
+    def mask_words(self, s):
+        return self.num_windows[s] * ((self.window_len[s] + 31) // 32)
+
+    def excise(self, ins, outs, masks=None, counts=None, stream=None):
+        check(rfi_excise(self.handle, ins, outs, masks, counts, stream), "rfi_excise")
+
+    def excise_host(self, ins, outs, masks=None, counts=None, stream=None):
+        check(rfi_excise_host(self.handle, ins, outs, masks, counts, stream), "rfi_excise_host")
+
+    def stats(self, medians=None, mads=None, stream=None):
+        st, t = rfi_stats(self.handle, medians, mads, stream)
+        return st, t
+
+    def info(self) -> RfiPlanInfo:
+        st, i = rfi_plan_get_info(self.handle)
+        check(st, "rfi_plan_get_info")
+        return i
+
+    def close(self):
+        if self.handle:
+            rfi_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,76 @@
+// Internal interface between the plan (host C++) and the excision kernels (CUDA).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rfi {
+
+// Bits that kernels OR into the plan's device status word.
+constexpr uint32_t kStatusSampleRange = 1u;  // reported as RFI_ERR_SAMPLE_RANGE
+constexpr uint32_t kStatusTimeout = 2u;      // reported as RFI_ERR_TIMEOUT
+
+// One contiguous run of windows of one stream, starting on a window boundary.
+struct Seg {
+    const uint8_t *in;    // sample 0 of the run
+    uint8_t *out;         // output sample 0
+    uint32_t *mask;       // mask block of window 0 (nullable)
+    uint32_t *counts;     // flagged count of window 0 (nullable)
+    int32_t *med;         // median of window 0 (nullable)
+    int32_t *mad;         // MAD of window 0 (nullable)
+    int64_t len;          // samples in the run
+    int64_t abs0;         // absolute stream index of sample 0 (multiple of W)
+    int32_t W;            // window length
+    uint32_t stream_id;   // Philox stream key
+    int32_t mask_words;   // ceil(W / 32)
+    int32_t vec;          // in/out 16-byte aligned and W * bytes_per_sample % 16 == 0
+};
+
+// Work-list entry of the persistent kernel: windows [w0, w0 + nw) of segment seg.
+struct Tile {
+    uint32_t seg;
+    uint32_t w0;
+    uint32_t nw;
+    uint32_t bytes;       // input bytes covered by the tile
+};
+
+// Method parameters shared by every window of a call.
+struct Params {
+    int64_t kq;                   // round(k * 1.4826 * 2^16)
+    uint64_t seed;                // noise key
+    int32_t cval;                 // constant replacement, already saturated
+    int32_t ncopies;              // 12-bit histogram copies (1, 2 or 4)
+    uint32_t *status;             // device status word (atomicOr of kStatus*)
+    unsigned long long *flagged;  // device total of flagged samples
+};
+
+struct Shape {
+    int consumer_warps;   // 4, 8 or 16
+    int stages;           // 1..8
+    int ctas_per_sm;      // 1..4
+    int stage_bytes;      // multiple of 128, >= the largest tile
+    int dynamic_tiles;    // 1: atomic counter, 2: static round robin
+    int hist_copies;      // 12-bit histogram copies
+};
+
+// Bytes of dynamic shared memory the kernels need.
+size_t persistent_smem_bytes(int bits, const Shape &s);
+size_t stream_smem_bytes(int bits, int consumer_warps, int ncopies, int window_bytes);
+
+// Maximum resident CTAs per SM of the persistent kernel for this shape (0 if it cannot run).
+int persistent_occupancy(int bits, int mode, const Shape &s);
+
+// Persistent batched kernel over a device work list. counter: one zeroed uint32 (dynamic tiles).
+cudaError_t launch_persistent(int bits, int mode, const Shape &s, int grid, const Seg *segs,
+                              const Tile *tiles, int ntiles, const Params &p, unsigned *counter,
+                              int inject_timeout, cudaStream_t st);
+
+// Plain kernel: one CTA per window of one segment (windows [w_begin, w_begin + nw)).
+cudaError_t launch_stream(int bits, int mode, int consumer_warps, const Seg &seg, int64_t w_begin,
+                          int64_t nw, const Params &p, cudaStream_t st);
+
+// Write n (<= kSegBatch) segment descriptors to dst (device) from kernel parameters.
+constexpr int kSegBatch = 32;
+cudaError_t launch_write_segs(Seg *dst, const Seg *src_host, int n, cudaStream_t st);
+
+}  // namespace rfi

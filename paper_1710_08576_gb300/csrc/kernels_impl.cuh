@@ -1,0 +1,297 @@
+// Excision kernels: the persistent batched kernel (bulk-copy pipeline, work list) and the plain
+// one-CTA-per-window kernel. Instantiated per sample width in kernels8.cu / kernels12.cu.
+#pragma once
+
+#include <mutex>
+
+#include "core.cuh"
+
+namespace rfi {
+namespace dev {
+
+constexpr int kMaxStages = 8;
+constexpr uint64_t kWaitTimeoutNs = 4000000000ull;   // 4 s: no healthy wait comes close
+constexpr uint64_t kInjectTimeoutNs = 1000000ull;    // 1 ms for the test hook
+
+__host__ __device__ constexpr int align_up(int v, int a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    int hist, cum, ctl, bar, meta, stage, total;
+};
+
+template <int BITS>
+__host__ __device__ inline Layout layout(int ncopies, int stages, int stage_bytes) {
+    Layout L;
+    L.hist = 0;
+    L.cum = align_up(Geo<BITS>::hist_bytes(ncopies), 128);
+    L.ctl = align_up(L.cum + Geo<BITS>::kCumWords * 4, 128);
+    L.bar = align_up(L.ctl + static_cast<int>(sizeof(Ctl)), 128);
+    L.meta = L.bar + (2 * kMaxStages + 1) * 8;
+    L.stage = align_up(L.meta + kMaxStages * 4, 128);
+    L.total = L.stage + stages * stage_bytes;
+    return L;
+}
+
+template <int BITS>
+__device__ __forceinline__ void zero_shared_state(const Shm &sm, int tid, int nthreads) {
+    uint4 *h = reinterpret_cast<uint4 *>(sm.hist);
+    const int n16 = Geo<BITS>::hist_bytes(sm.ncopies) / 16;
+    for (int i = tid; i < n16; i += nthreads) h[i] = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t *c = reinterpret_cast<uint32_t *>(sm.ctl);
+    for (int i = tid; i < static_cast<int>(sizeof(Ctl) / 4); i += nthreads) c[i] = 0u;
+}
+
+__device__ __forceinline__ Win make_win(const Seg &sg, int64_t w, const uint8_t *data, int bps) {
+    Win win;
+    const int64_t s0 = w * sg.W;
+    const int64_t left = sg.len - s0;
+    win.data = data;
+    win.n = static_cast<int32_t>(left < sg.W ? left : sg.W);
+    win.out = sg.out + s0 * bps;
+    win.mask = sg.mask ? sg.mask + w * sg.mask_words : nullptr;
+    win.mask_words = sg.mask_words;
+    win.abs_idx = sg.abs0 + s0;
+    win.sid = sg.stream_id;
+    win.vec = sg.vec != 0;
+    win.count_out = sg.counts ? sg.counts + w : nullptr;
+    win.med_out = sg.med ? sg.med + w : nullptr;
+    win.mad_out = sg.mad ? sg.mad + w : nullptr;
+    return win;
+}
+
+// ------------------------------------------------------------------ persistent kernel
+// Warps 0..CW-1 process windows; warp CW is the copy warp. Stage s of the shared ring holds one
+// tile; full[s] completes when its bytes have landed (bulk copy + transaction count), empty[s]
+// when the consumers are done with it. All waits are bounded.
+template <int BITS, int MODE, int CW>
+__global__ void __launch_bounds__((CW + 1) * 32)
+persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, int ntiles, Params p,
+                  int stages, int stage_bytes, int dynamic_tiles, unsigned *counter, int inject_timeout) {
+    constexpr int T = CW * 32;
+    constexpr int BPS = Geo<BITS>::kBps;
+    extern __shared__ __align__(128) uint8_t smem[];
+    const Layout L = layout<BITS>(p.ncopies, stages, stage_bytes);
+    Shm sm;
+    sm.hist = smem + L.hist;
+    sm.hist_s = smem_addr(sm.hist);
+    sm.cum = reinterpret_cast<uint32_t *>(smem + L.cum);
+    sm.ctl = reinterpret_cast<Ctl *>(smem + L.ctl);
+    sm.ncopies = p.ncopies;
+    const uint32_t bar0 = smem_addr(smem + L.bar);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (kMaxStages + s); };
+    const uint32_t inj_bar = bar0 + 8u * (2 * kMaxStages);
+    int *meta = reinterpret_cast<int *>(smem + L.meta);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        mbar_init(inj_bar, 1);
+        fence_mbar_init();
+    }
+    zero_shared_state<BITS>(sm, tid, blockDim.x);
+    __syncthreads();
+
+    if (warp == CW) {
+        // ---------------- copy warp
+        int issued = 0;  // iterations whose full barrier was armed
+        for (int it = 0;; ++it) {
+            const int s = it % stages;
+            const int u = it / stages;
+            if (u > 0) {
+                int ok = 1;
+                if (lane == 0) ok = mbar_wait_bounded(empty_bar(s), (u - 1) & 1, kWaitTimeoutNs);
+                ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+                if (!ok) {
+                    if (lane == 0) {
+                        atomicOr(p.status, kStatusTimeout);
+                        atomicExch(&sm.ctl->abort, 1u);
+                    }
+                    break;
+                }
+            }
+            if (*reinterpret_cast<volatile uint32_t *>(&sm.ctl->abort)) break;
+            int t = 0;
+            if (lane == 0)
+                t = dynamic_tiles == 1 ? static_cast<int>(atomicAdd(counter, 1u))
+                                       : static_cast<int>(blockIdx.x + static_cast<unsigned>(it) * gridDim.x);
+            t = __shfl_sync(0xFFFFFFFFu, t, 0);
+            issued = it + 1;
+            if (t >= ntiles) {
+                if (lane == 0) {
+                    meta[s] = -1;
+                    mbar_arrive(full_bar(s));
+                }
+                break;
+            }
+            const Tile tl = tiles[t];
+            const Seg &sg = segs[tl.seg];
+            uint8_t *stage = smem + L.stage + s * stage_bytes;
+            if (sg.vec) {
+                const uint8_t *src = sg.in + static_cast<int64_t>(tl.w0) * sg.W * BPS;
+                const uint32_t bulk = tl.bytes & ~15u, rem = tl.bytes & 15u;
+                if (static_cast<uint32_t>(lane) < rem) stage[bulk + lane] = src[bulk + lane];
+                __syncwarp();
+                if (lane == 0) {
+                    meta[s] = t;
+                    mbar_arrive_tx(full_bar(s), bulk);
+                    if (bulk) bulk_g2s(smem_addr(stage), src, bulk, full_bar(s));
+                }
+            } else if (lane == 0) {
+                meta[s] = t;
+                mbar_arrive(full_bar(s));
+            }
+        }
+        // drain: every armed stage has landed before the copy warp leaves
+        if (lane == 0) {
+            for (int i = issued - stages < 0 ? 0 : issued - stages; i < issued; ++i)
+                mbar_wait_bounded(full_bar(i % stages), (i / stages) & 1, kWaitTimeoutNs);
+        }
+        return;
+    }
+
+    // ---------------- consumer warps
+    if (inject_timeout && blockIdx.x == 0 && tid == 0) {
+        if (!mbar_wait_bounded(inj_bar, 0, kInjectTimeoutNs)) atomicOr(p.status, kStatusTimeout);
+    }
+    for (int it = 0;; ++it) {
+        const int s = it % stages;
+        const int u = it / stages;
+        if (tid == 0) {
+            const bool ok = mbar_wait_bounded(full_bar(s), u & 1, kWaitTimeoutNs);
+            sm.ctl->go = ok ? meta[s] : -2;
+            if (!ok) {
+                atomicOr(p.status, kStatusTimeout);
+                atomicExch(&sm.ctl->abort, 1u);
+            }
+        }
+        named_bar(1, T);
+        const int t = *reinterpret_cast<volatile int *>(&sm.ctl->go);
+        if (t == -2) break;
+        mbar_try_wait(full_bar(s), u & 1);  // phase is complete: acquire for this thread
+        if (t < 0) break;
+        const Tile tl = tiles[t];
+        const Seg &sg = segs[tl.seg];
+        uint8_t *stage = smem + L.stage + s * stage_bytes;
+        if (!sg.vec) {
+            const uint8_t *src = sg.in + static_cast<int64_t>(tl.w0) * sg.W * BPS;
+            for (int i = tid; i < static_cast<int>(tl.bytes); i += T) stage[i] = src[i];
+            named_bar(1, T);
+        }
+        for (uint32_t k = 0; k < tl.nw; ++k) {
+            const Win win = make_win(sg, static_cast<int64_t>(tl.w0) + k, stage + k * sg.W * BPS, BPS);
+            process_window<BITS, MODE, T>(sm, win, p, tid);
+        }
+        if (tid == 0) mbar_arrive(empty_bar(s));
+    }
+    if (tid == 0 && sm.ctl->flagged) atomicAdd(p.flagged, sm.ctl->flagged);
+}
+
+// ------------------------------------------------------------------ plain kernel
+template <int BITS, int MODE, int CW>
+__global__ void __launch_bounds__(CW * 32) stream_kernel(Seg sg, int64_t w_begin, Params p) {
+    constexpr int T = CW * 32;
+    constexpr int BPS = Geo<BITS>::kBps;
+    extern __shared__ __align__(128) uint8_t smem[];
+    const Layout L = layout<BITS>(p.ncopies, 1, 0);
+    Shm sm;
+    sm.hist = smem + L.hist;
+    sm.hist_s = smem_addr(sm.hist);
+    sm.cum = reinterpret_cast<uint32_t *>(smem + L.cum);
+    sm.ctl = reinterpret_cast<Ctl *>(smem + L.ctl);
+    sm.ncopies = p.ncopies;
+    const int tid = threadIdx.x;
+    uint8_t *buf = smem + L.stage;
+    zero_shared_state<BITS>(sm, tid, T);
+    const int64_t w = w_begin + blockIdx.x;
+    const int64_t s0 = w * sg.W;
+    const int n = static_cast<int>(sg.len - s0 < sg.W ? sg.len - s0 : sg.W);
+    const int nbytes = n * BPS;
+    const uint8_t *src = sg.in + s0 * BPS;
+    if (sg.vec) {
+        const int nfull = nbytes >> 4;
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *b4 = reinterpret_cast<uint4 *>(buf);
+        for (int c = tid; c < nfull; c += T) b4[c] = __ldcs(s4 + c);
+        for (int i = nfull * 16 + tid; i < nbytes; i += T) buf[i] = src[i];
+    } else {
+        for (int i = tid; i < nbytes; i += T) buf[i] = src[i];
+    }
+    __syncthreads();
+    const Win win = make_win(sg, w, buf, BPS);
+    process_window<BITS, MODE, T>(sm, win, p, tid);
+    if (tid == 0 && sm.ctl->flagged) atomicAdd(p.flagged, sm.ctl->flagged);
+}
+
+// ------------------------------------------------------------------ host-side dispatch
+// Raise the dynamic shared-memory cap of one kernel instantiation, once per process. The tag
+// parameters make the static once-flag distinct for every instantiation.
+template <int KIND, int BITS, int MODE, int CW, typename K>
+inline cudaError_t allow_smem(K kernel) {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [&] {
+        err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    });
+    return err;
+}
+
+template <int BITS, int MODE, int CW>
+cudaError_t persistent_launch_t(const Shape &s, int grid, const Seg *segs, const Tile *tiles, int ntiles,
+                                const Params &p, unsigned *counter, int inject, cudaStream_t st) {
+    auto k = persistent_kernel<BITS, MODE, CW>;
+    cudaError_t e = allow_smem<0, BITS, MODE, CW>(k);
+    if (e != cudaSuccess) return e;
+    const Layout L = layout<BITS>(p.ncopies, s.stages, s.stage_bytes);
+    k<<<grid, (CW + 1) * 32, L.total, st>>>(segs, tiles, ntiles, p, s.stages, s.stage_bytes, s.dynamic_tiles,
+                                            counter, inject);
+    return cudaGetLastError();
+}
+
+template <int BITS, int MODE, int CW>
+int persistent_occ_t(const Shape &s) {
+    auto k = persistent_kernel<BITS, MODE, CW>;
+    if (allow_smem<0, BITS, MODE, CW>(k) != cudaSuccess) return 0;
+    const Layout L = layout<BITS>(s.hist_copies, s.stages, s.stage_bytes);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, (CW + 1) * 32, L.total) != cudaSuccess) return 0;
+    return n;
+}
+
+template <int BITS, int MODE, int CW>
+cudaError_t stream_launch_t(const Seg &sg, int64_t w_begin, int64_t nw, const Params &p, cudaStream_t st) {
+    auto k = stream_kernel<BITS, MODE, CW>;
+    cudaError_t e = allow_smem<1, BITS, MODE, CW>(k);
+    if (e != cudaSuccess) return e;
+    const Layout L = layout<BITS>(p.ncopies, 1, align_up(sg.W * Geo<BITS>::kBps, 128));
+    for (int64_t b = 0; b < nw; b += 0x7FFFFFFF) {
+        const int64_t g = nw - b < 0x7FFFFFFF ? nw - b : 0x7FFFFFFF;
+        k<<<static_cast<unsigned>(g), CW * 32, L.total, st>>>(sg, w_begin + b, p);
+    }
+    return cudaGetLastError();
+}
+
+#define RFI_DISPATCH_MODE_CW(BITS, FN, MODE, CW, ...)                                          \
+    do {                                                                                       \
+        switch (MODE * 100 + CW) {                                                             \
+            case 4: return FN<BITS, 0, 4>(__VA_ARGS__);                                        \
+            case 8: return FN<BITS, 0, 8>(__VA_ARGS__);                                        \
+            case 16: return FN<BITS, 0, 16>(__VA_ARGS__);                                      \
+            case 104: return FN<BITS, 1, 4>(__VA_ARGS__);                                      \
+            case 108: return FN<BITS, 1, 8>(__VA_ARGS__);                                      \
+            case 116: return FN<BITS, 1, 16>(__VA_ARGS__);                                     \
+            case 204: return FN<BITS, 2, 4>(__VA_ARGS__);                                      \
+            case 208: return FN<BITS, 2, 8>(__VA_ARGS__);                                      \
+            case 216: return FN<BITS, 2, 16>(__VA_ARGS__);                                     \
+            case 304: return FN<BITS, 3, 4>(__VA_ARGS__);                                      \
+            case 308: return FN<BITS, 3, 8>(__VA_ARGS__);                                      \
+            case 316: return FN<BITS, 3, 16>(__VA_ARGS__);                                     \
+            default: break;                                                                    \
+        }                                                                                      \
+    } while (0)
+
+}  // namespace dev
+}  // namespace rfi

@@ -1,0 +1,389 @@
+// librfi C ABI: plans, the batched and per-stream excision calls, statistics and the host
+// pipelined variant. Semantics are stated in include/rfi.h.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "rfi.h"
+#include "internal.h"
+#include "plan_impl.h"
+
+namespace {
+
+using rfi::Seg;
+using rfi::Shape;
+using rfi::Tile;
+
+rfi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RFI_OK : RFI_ERR_CUDA; }
+
+#define RFI_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return RFI_ERR_CUDA;      \
+    } while (0)
+
+bool valid_shape(const rfi_launch_shape &s) {
+    return s.consumer_warps >= 0 && s.stages >= 0 && s.stages <= 8 && s.ctas_per_sm >= 0 &&
+           s.ctas_per_sm <= 4 && s.stage_bytes >= 0 && s.stage_bytes <= 227 * 1024 && s.dynamic_tiles >= 0 &&
+           s.dynamic_tiles <= 2 && s.hist_copies >= 0 && s.hist_copies <= 4 && s.hist_copies != 3 &&
+           (s.consumer_warps == 0 || s.consumer_warps == 4 || s.consumer_warps == 8 || s.consumer_warps == 16);
+}
+
+}  // namespace
+
+namespace rfi {
+
+rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req) {
+    Shape s;
+    const int bps = P->bits == 8 ? 1 : 2;
+    int64_t maxwb = 0;
+    bool uniform = true;
+    for (int i = 0; i < P->S; ++i) {
+        const int64_t first = std::min<int64_t>(P->W[i], P->len[i]) * bps;
+        maxwb = std::max<int64_t>(maxwb, first);
+        if (P->W[i] != P->W[0]) uniform = false;
+    }
+    const int min_stage = static_cast<int>((maxwb + 127) / 128 * 128);
+    s.consumer_warps = (req && req->consumer_warps) ? req->consumer_warps : 8;
+    s.stage_bytes = std::max(min_stage, (req && req->stage_bytes) ? req->stage_bytes : 16384);
+    s.stage_bytes = (s.stage_bytes + 127) / 128 * 128;
+    s.stages = (req && req->stages) ? req->stages : std::max(2, std::min(6, 65536 / s.stage_bytes));
+    s.hist_copies = P->bits == 8 ? 1 : ((req && req->hist_copies) ? req->hist_copies : 2);
+    s.dynamic_tiles = (req && req->dynamic_tiles) ? req->dynamic_tiles : (uniform ? 2 : 1);
+    const int want_ctas = (req && req->ctas_per_sm) ? req->ctas_per_sm : 2;
+    if (persistent_smem_bytes(P->bits, s) > 227u * 1024u) {
+        if (req && req->stages) return RFI_ERR_UNSUPPORTED;
+        while (s.stages > 1 && persistent_smem_bytes(P->bits, s) > 227u * 1024u) --s.stages;
+        if (persistent_smem_bytes(P->bits, s) > 227u * 1024u) return RFI_ERR_UNSUPPORTED;
+    }
+    const int occ = persistent_occupancy(P->bits, P->mode, s);
+    if (occ < 1) return cudaGetLastError() != cudaSuccess ? RFI_ERR_CUDA : RFI_ERR_UNSUPPORTED;
+    s.ctas_per_sm = std::min(want_ctas, occ);
+    P->shape = s;
+    return RFI_OK;
+}
+
+rfi_status plan_build_tiles(rfi_plan_s *P) {
+    const int bps = P->bits == 8 ? 1 : 2;
+    std::vector<Tile> tiles;
+    for (int i = 0; i < P->S; ++i) {
+        const int64_t wb = static_cast<int64_t>(P->W[i]) * bps;
+        const int64_t per = (wb % 16 == 0) ? std::max<int64_t>(1, P->shape.stage_bytes / wb) : 1;
+        for (int64_t w0 = 0; w0 < P->nwin[i]; w0 += per) {
+            const int64_t nw = std::min<int64_t>(per, P->nwin[i] - w0);
+            const int64_t s0 = w0 * P->W[i];
+            const int64_t s1 = std::min<int64_t>(P->len[i], (w0 + nw) * P->W[i]);
+            Tile t;
+            t.seg = static_cast<uint32_t>(i);
+            t.w0 = static_cast<uint32_t>(w0);
+            t.nw = static_cast<uint32_t>(nw);
+            t.bytes = static_cast<uint32_t>((s1 - s0) * bps);
+            tiles.push_back(t);
+        }
+    }
+    // largest tiles first (a longest-processing-time order for the dynamic queue); stable keeps
+    // each stream's tiles in stream order
+    std::stable_sort(tiles.begin(), tiles.end(), [](const Tile &a, const Tile &b) { return a.bytes > b.bytes; });
+    if (tiles.size() > 0x7FFFFFFFu) return RFI_ERR_UNSUPPORTED;
+    P->tiles_host = std::move(tiles);
+    P->ntiles = static_cast<int>(P->tiles_host.size());
+    P->grid = std::max(1, std::min(P->ntiles, P->sm_count * P->shape.ctas_per_sm));
+    return RFI_OK;
+}
+
+rfi_status plan_alloc_workspace(rfi_plan_s *P) {
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t seg_b = al(sizeof(Seg) * P->S);
+    const size_t tile_b = al(sizeof(Tile) * P->tiles_host.size());
+    const size_t md_b = al(sizeof(int32_t) * P->total_windows);
+    const size_t ctr_b = 256;
+    P->ws_bytes = seg_b + tile_b + 2 * md_b + ctr_b;
+    if (P->ws) cudaFree(P->ws);
+    P->ws = nullptr;
+    if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        P->ws = nullptr;
+        return RFI_ERR_OOM;
+    }
+    uint8_t *b = static_cast<uint8_t *>(P->ws);
+    P->d_ctr = reinterpret_cast<DevCounters *>(b);
+    P->d_segs = reinterpret_cast<Seg *>(b + ctr_b);
+    P->d_tiles = reinterpret_cast<Tile *>(b + ctr_b + seg_b);
+    P->d_med = reinterpret_cast<int32_t *>(b + ctr_b + seg_b + tile_b);
+    P->d_mad = reinterpret_cast<int32_t *>(b + ctr_b + seg_b + tile_b + md_b);
+    RFI_CUDA(cudaMemset(P->ws, 0, P->ws_bytes));
+    RFI_CUDA(cudaMemcpy(P->d_tiles, P->tiles_host.data(), sizeof(Tile) * P->tiles_host.size(),
+                        cudaMemcpyHostToDevice));
+    P->segs_valid = false;
+    return RFI_OK;
+}
+
+Params plan_params(const rfi_plan_s *P) {
+    Params p;
+    p.kq = P->kq;
+    p.seed = P->seed;
+    p.cval = P->cval;
+    p.ncopies = P->shape.hist_copies;
+    p.status = &P->d_ctr->status;
+    p.flagged = &P->d_ctr->flagged;
+    return p;
+}
+
+// Enqueue the persistent launch (with its counter reset) on st.
+rfi_status plan_enqueue_batched(rfi_plan_s *P, cudaStream_t st) {
+    RFI_CUDA(cudaMemsetAsync(P->d_ctr, 0, sizeof(DevCounters), st));
+    RFI_CUDA(launch_persistent(P->bits, P->mode, P->shape, P->grid, P->d_segs, P->d_tiles, P->ntiles,
+                               plan_params(P), &P->d_ctr->tile_counter,
+                               (P->flags & RFI_PLAN_INJECT_TIMEOUT) ? 1 : 0, st));
+    return RFI_OK;
+}
+
+rfi_status plan_build_graph(rfi_plan_s *P) {
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    P->gexec = nullptr;
+    P->graph = nullptr;
+    cudaStream_t cs;
+    RFI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    rfi_status rs = RFI_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rs = RFI_ERR_CUDA;
+    } else {
+        rs = plan_enqueue_batched(P, cs);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (rs == RFI_OK && e != cudaSuccess) rs = RFI_ERR_CUDA;
+        if (rs == RFI_OK && cudaGraphInstantiate(&P->gexec, g, 0) != cudaSuccess) rs = RFI_ERR_CUDA;
+        if (rs == RFI_OK) P->graph = g;
+        else if (g) cudaGraphDestroy(g);
+    }
+    cudaStreamDestroy(cs);
+    return rs;
+}
+
+std::vector<Seg> plan_segs(const rfi_plan_s *P, const void *const *in, void *const *out, uint32_t *const *mask,
+                           uint32_t *const *counts) {
+    const int bps = P->bits == 8 ? 1 : 2;
+    std::vector<Seg> segs(P->S);
+    for (int i = 0; i < P->S; ++i) {
+        Seg &g = segs[i];
+        std::memset(&g, 0, sizeof(Seg));
+        g.in = static_cast<const uint8_t *>(in[i]);
+        g.out = static_cast<uint8_t *>(out[i]);
+        g.mask = mask ? mask[i] : nullptr;
+        g.counts = counts ? counts[i] : nullptr;
+        g.med = P->d_med + P->woff[i];
+        g.mad = P->d_mad + P->woff[i];
+        g.len = P->len[i];
+        g.abs0 = 0;
+        g.W = P->W[i];
+        g.stream_id = P->sid[i];
+        g.mask_words = (P->W[i] + 31) / 32;
+        g.vec = ((reinterpret_cast<uintptr_t>(in[i]) | reinterpret_cast<uintptr_t>(out[i])) % 16 == 0) &&
+                (static_cast<int64_t>(P->W[i]) * bps) % 16 == 0;
+    }
+    return segs;
+}
+
+rfi_status plan_check_buffers(const rfi_plan_s *P, const void *const *in, void *const *out,
+                              uint32_t *const *mask, uint32_t *const *counts) {
+    if (!in || !out) return RFI_ERR_INVALID_ARG;
+    for (int i = 0; i < P->S; ++i) {
+        if (!in[i] || !out[i]) return RFI_ERR_INVALID_ARG;
+        if (P->bits == 12 && ((reinterpret_cast<uintptr_t>(in[i]) | reinterpret_cast<uintptr_t>(out[i])) & 1))
+            return RFI_ERR_ALIGNMENT;
+        if (mask && mask[i] && (reinterpret_cast<uintptr_t>(mask[i]) & 3)) return RFI_ERR_ALIGNMENT;
+        if (counts && counts[i] && (reinterpret_cast<uintptr_t>(counts[i]) & 3)) return RFI_ERR_ALIGNMENT;
+    }
+    return RFI_OK;
+}
+
+}  // namespace rfi
+
+using namespace rfi;
+
+extern "C" {
+
+const char *rfi_version(void) { return "librfi 1.0 (sm_103a)"; }
+
+const char *rfi_status_string(rfi_status s) {
+    switch (s) {
+        case RFI_OK: return "ok";
+        case RFI_ERR_INVALID_ARG: return "invalid argument";
+        case RFI_ERR_UNSUPPORTED: return "unsupported request";
+        case RFI_ERR_ALIGNMENT: return "misaligned buffer";
+        case RFI_ERR_OOM: return "out of memory or over budget";
+        case RFI_ERR_CUDA: return "CUDA runtime error";
+        case RFI_ERR_SAMPLE_RANGE: return "12-bit sample outside [-2048, 2047]";
+        case RFI_ERR_TIMEOUT: return "bounded device wait timed out";
+        case RFI_ERR_BUSY: return "busy: no free slot";
+    }
+    return "unknown status";
+}
+
+rfi_status rfi_plan_create(const rfi_plan_desc *d, rfi_plan_t *out_plan) {
+    if (!d || !out_plan) return RFI_ERR_INVALID_ARG;
+    *out_plan = nullptr;
+    if (d->sample_bits != 8 && d->sample_bits != 12) return RFI_ERR_INVALID_ARG;
+    if (d->num_streams < 1 || !d->stream_len || !d->window_len) return RFI_ERR_INVALID_ARG;
+    if (!(d->k > 0.0) || !std::isfinite(d->k) || d->k > 1.0e6) return RFI_ERR_INVALID_ARG;
+    if (d->mode < RFI_REPLACE_ZERO || d->mode > RFI_REPLACE_NOISE) return RFI_ERR_INVALID_ARG;
+    const uint32_t known = RFI_PLAN_PER_STREAM | RFI_PLAN_BATCHED | RFI_PLAN_GRAPH | RFI_PLAN_AUTOTUNE |
+                           RFI_PLAN_INJECT_TIMEOUT;
+    if (d->flags & ~known) return RFI_ERR_INVALID_ARG;
+    if ((d->flags & RFI_PLAN_PER_STREAM) && (d->flags & (RFI_PLAN_BATCHED | RFI_PLAN_GRAPH)))
+        return RFI_ERR_INVALID_ARG;
+    if (d->shape && !valid_shape(*d->shape)) return RFI_ERR_INVALID_ARG;
+    // Kq = round_half_up(k * 1.4826 * 2^16) (fixed-point multiple of Eq. 1)
+    const int64_t kq = static_cast<int64_t>(std::floor(d->k * 1.4826 * 65536.0 + 0.5));
+    if (kq < 1) return RFI_ERR_INVALID_ARG;
+    uint64_t total_w = 0, total_s = 0;
+    for (int i = 0; i < d->num_streams; ++i) {
+        if (d->stream_len[i] < 1 || d->window_len[i] < 1 || d->window_len[i] > 65536) return RFI_ERR_INVALID_ARG;
+        const int64_t nw = (d->stream_len[i] + d->window_len[i] - 1) / d->window_len[i];
+        if (nw > 0x7FFFFFFF) return RFI_ERR_UNSUPPORTED;
+        total_w += static_cast<uint64_t>(nw);
+        total_s += static_cast<uint64_t>(d->stream_len[i]);
+    }
+    if (total_w > 0x7FFFFFFFull) return RFI_ERR_UNSUPPORTED;
+
+    rfi_plan_s *P = new (std::nothrow) rfi_plan_s();
+    if (!P) return RFI_ERR_OOM;
+    P->bits = d->sample_bits;
+    P->S = d->num_streams;
+    P->mode = d->mode;
+    P->flags = d->flags;
+    P->k = d->k;
+    P->kq = kq;
+    const int32_t lo = P->bits == 8 ? -128 : -2048, hi = P->bits == 8 ? 127 : 2047;
+    P->cval = std::min(hi, std::max(lo, d->const_value));
+    P->seed = d->seed;
+    P->len.assign(d->stream_len, d->stream_len + P->S);
+    P->W.assign(d->window_len, d->window_len + P->S);
+    P->sid.resize(P->S);
+    for (int i = 0; i < P->S; ++i) P->sid[i] = d->stream_id ? d->stream_id[i] : static_cast<uint32_t>(i);
+    P->nwin.resize(P->S);
+    P->woff.resize(P->S);
+    int64_t acc = 0;
+    for (int i = 0; i < P->S; ++i) {
+        P->nwin[i] = (P->len[i] + P->W[i] - 1) / P->W[i];
+        P->woff[i] = acc;
+        acc += P->nwin[i];
+    }
+    P->total_windows = total_w;
+    P->total_samples = total_s;
+
+    rfi_status rs = RFI_OK;
+    if (cudaGetDevice(&P->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        return RFI_ERR_CUDA;
+    }
+    rs = plan_choose_shape(P, d->shape);
+    if (rs == RFI_OK) rs = plan_build_tiles(P);
+    if (rs == RFI_OK) rs = plan_alloc_workspace(P);
+    if (rs == RFI_OK && (P->flags & RFI_PLAN_AUTOTUNE) && !(P->flags & RFI_PLAN_PER_STREAM))
+        rs = plan_autotune(P, d->shape);
+    if (rs == RFI_OK && (P->flags & RFI_PLAN_GRAPH)) rs = plan_build_graph(P);
+    if (rs != RFI_OK) {
+        rfi_plan_destroy(P);
+        return rs;
+    }
+    *out_plan = P;
+    return RFI_OK;
+}
+
+rfi_status rfi_excise(rfi_plan_t P, const void *const *in, void *const *out, uint32_t *const *mask,
+                      uint32_t *const *counts, void *stream) {
+    if (!P) return RFI_ERR_INVALID_ARG;
+    rfi_status rs = plan_check_buffers(P, in, out, mask, counts);
+    if (rs != RFI_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<Seg> segs = plan_segs(P, in, out, mask, counts);
+    P->last_windows = P->total_windows;
+    if (P->flags & RFI_PLAN_PER_STREAM) {
+        RFI_CUDA(cudaMemsetAsync(P->d_ctr, 0, sizeof(DevCounters), st));
+        const Params p = plan_params(P);
+        for (int i = 0; i < P->S; ++i)
+            RFI_CUDA(launch_stream(P->bits, P->mode, P->shape.consumer_warps, segs[i], 0, P->nwin[i], p, st));
+        return RFI_OK;
+    }
+    if (!P->segs_valid || std::memcmp(segs.data(), P->segs_host.data(), sizeof(Seg) * P->S) != 0) {
+        for (int i = 0; i < P->S; i += kSegBatch)
+            RFI_CUDA(launch_write_segs(P->d_segs + i, segs.data() + i, std::min(kSegBatch, P->S - i), st));
+        P->segs_host = segs;
+        P->segs_valid = true;
+        P->last_seg_writes = (P->S + kSegBatch - 1) / kSegBatch;
+    } else {
+        P->last_seg_writes = 0;
+    }
+    if (P->gexec) {
+        RFI_CUDA(cudaGraphLaunch(P->gexec, st));
+        return RFI_OK;
+    }
+    return plan_enqueue_batched(P, st);
+}
+
+rfi_status rfi_stats(rfi_plan_t P, int32_t *const *median, int32_t *const *mad, rfi_totals *totals, void *stream) {
+    if (!P) return RFI_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int i = 0; i < P->S; ++i) {
+        const size_t b = sizeof(int32_t) * P->nwin[i];
+        if (median && median[i])
+            RFI_CUDA(cudaMemcpyAsync(median[i], P->d_med + P->woff[i], b, cudaMemcpyDeviceToDevice, st));
+        if (mad && mad[i])
+            RFI_CUDA(cudaMemcpyAsync(mad[i], P->d_mad + P->woff[i], b, cudaMemcpyDeviceToDevice, st));
+    }
+    DevCounters h;
+    RFI_CUDA(cudaMemcpyAsync(&h, P->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    RFI_CUDA(cudaStreamSynchronize(st));
+    const rfi_status dev = (h.status & kStatusTimeout) ? RFI_ERR_TIMEOUT
+                           : (h.status & kStatusSampleRange) ? RFI_ERR_SAMPLE_RANGE
+                                                             : RFI_OK;
+    if (totals) {
+        totals->windows = P->last_windows;
+        totals->flagged = h.flagged;
+        totals->device_status = static_cast<int32_t>(dev);
+    }
+    return dev;
+}
+
+rfi_status rfi_plan_get_info(rfi_plan_t P, rfi_plan_info *info) {
+    if (!P || !info) return RFI_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->k_q16 = P->kq;
+    info->total_windows = P->total_windows;
+    info->total_samples = P->total_samples;
+    info->workspace_bytes = P->ws_bytes + P->host_pipe_bytes;
+    info->tiles = P->ntiles;
+    info->grid = P->grid;
+    info->shape.consumer_warps = P->shape.consumer_warps;
+    info->shape.stages = P->shape.stages;
+    info->shape.ctas_per_sm = P->shape.ctas_per_sm;
+    info->shape.stage_bytes = P->shape.stage_bytes;
+    info->shape.dynamic_tiles = P->shape.dynamic_tiles;
+    info->shape.hist_copies = P->shape.hist_copies;
+    info->sm_count = P->sm_count;
+    info->kernels_per_call = (P->flags & RFI_PLAN_PER_STREAM) ? P->S : 1;
+    return RFI_OK;
+}
+
+rfi_status rfi_plan_destroy(rfi_plan_t P) {
+    if (!P) return RFI_OK;
+    plan_release_host_pipe(P);
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->ws) cudaFree(P->ws);
+    cudaGetLastError();
+    delete P;
+    return RFI_OK;
+}
+
+}  // extern "C"

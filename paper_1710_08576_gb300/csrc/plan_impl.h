@@ -1,0 +1,83 @@
+// Host-side plan state shared by plan.cpp, host_pipe.cpp and autotune.cpp.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "rfi.h"
+#include "internal.h"
+
+namespace rfi {
+
+// Device counters reset before every call.
+struct DevCounters {
+    unsigned tile_counter;       // dynamic work-list cursor
+    uint32_t status;             // kStatus* bits
+    unsigned long long flagged;  // flagged samples of the call
+};
+
+// Buffers of the chunked host pipeline (rfi_excise_host), allocated on first use.
+struct HostPipe {
+    static constexpr int kSlots = 3;
+    int64_t chunk_bytes = 0;     // input bytes per slot
+    uint8_t *in[kSlots] = {};
+    uint8_t *out[kSlots] = {};
+    uint32_t *mask[kSlots] = {};
+    uint32_t *counts[kSlots] = {};
+    cudaEvent_t h2d[kSlots] = {}, comp[kSlots] = {}, d2h[kSlots] = {};
+    cudaStream_t s_comp = nullptr, s_d2h = nullptr;
+    bool ready = false;
+};
+
+}  // namespace rfi
+
+struct rfi_plan_s {
+    int bits = 8, S = 0, mode = 0;
+    uint32_t flags = 0;
+    double k = 0;
+    int64_t kq = 0;
+    int32_t cval = 0;
+    uint64_t seed = 0;
+    std::vector<int64_t> len;
+    std::vector<int32_t> W;
+    std::vector<uint32_t> sid;
+    std::vector<int64_t> nwin, woff;
+    uint64_t total_windows = 0, total_samples = 0, last_windows = 0;
+    int device = 0, sm_count = 0;
+    rfi::Shape shape{};
+    std::vector<rfi::Tile> tiles_host;
+    int ntiles = 0, grid = 0;
+    // device workspace
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    rfi::DevCounters *d_ctr = nullptr;
+    rfi::Seg *d_segs = nullptr;
+    rfi::Tile *d_tiles = nullptr;
+    int32_t *d_med = nullptr, *d_mad = nullptr;
+    std::vector<rfi::Seg> segs_host;
+    bool segs_valid = false;
+    int last_seg_writes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    rfi::HostPipe pipe;
+    size_t host_pipe_bytes = 0;
+};
+
+namespace rfi {
+
+rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req);
+rfi_status plan_build_tiles(rfi_plan_s *P);
+rfi_status plan_alloc_workspace(rfi_plan_s *P);
+rfi_status plan_enqueue_batched(rfi_plan_s *P, cudaStream_t st);
+rfi_status plan_build_graph(rfi_plan_s *P);
+rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req);
+void plan_release_host_pipe(rfi_plan_s *P);
+Params plan_params(const rfi_plan_s *P);
+std::vector<Seg> plan_segs(const rfi_plan_s *P, const void *const *in, void *const *out, uint32_t *const *mask,
+                           uint32_t *const *counts);
+rfi_status plan_check_buffers(const rfi_plan_s *P, const void *const *in, void *const *out,
+                              uint32_t *const *mask, uint32_t *const *counts);
+
+}  // namespace rfi

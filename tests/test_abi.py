@@ -1,0 +1,94 @@
+"""The C ABI without a GPU: the library loads, exports what include/rfi.h declares, its structs
+match the header's layout, and argument errors come back before any CUDA call."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1710_08576_gb300 as rfi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rfi.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"RFI_API\s+[\w\s\*]*?\b(rfi_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for n in ("rfi_plan_create", "rfi_excise", "rfi_stats", "rfi_plan_destroy", "rfi_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(rfi.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_only_the_abi_is_exported():
+    out = subprocess.run(["nm", "-D", "--defined-only", rfi.LIB_PATH], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("nm unavailable")
+    text_syms = {l.split()[-1] for l in out.stdout.splitlines() if " T " in l}
+    assert text_syms == set(declared_functions())
+
+
+def test_struct_layout_matches_header(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "rfi.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(rfi_launch_shape), sizeof(rfi_plan_desc),
+         sizeof(rfi_totals), sizeof(rfi_plan_info), offsetof(rfi_plan_desc, shape));
+  printf("%zu %zu %zu\n", offsetof(rfi_plan_desc, k), offsetof(rfi_plan_desc, seed),
+         offsetof(rfi_plan_info, shape));
+  return 0;
+}''')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    a, b = subprocess.check_output([str(exe)], text=True).splitlines()
+    C = ctypes
+    assert [int(v) for v in a.split()] == [C.sizeof(rfi.RfiLaunchShape), C.sizeof(rfi.RfiPlanDesc),
+                                          C.sizeof(rfi.RfiTotals), C.sizeof(rfi.RfiPlanInfo),
+                                          rfi.RfiPlanDesc.shape.offset]
+    assert [int(v) for v in b.split()] == [rfi.RfiPlanDesc.k.offset, rfi.RfiPlanDesc.seed.offset,
+                                          rfi.RfiPlanInfo.shape.offset]
+
+
+@pytest.mark.parametrize("kw", [
+    dict(bits=7), dict(bits=16), dict(stream_len=[0]), dict(window_len=[0]),
+    dict(window_len=[65537]), dict(k=0.0), dict(k=-3.0), dict(k=float("nan")), dict(k=1e-7),
+    dict(mode=4), dict(mode=-1), dict(flags=0x80000000),
+    dict(flags=rfi.RFI_PLAN_PER_STREAM | rfi.RFI_PLAN_GRAPH),
+    dict(shape=dict(consumer_warps=5)), dict(shape=dict(stages=9)), dict(shape=dict(hist_copies=3)),
+])
+def test_invalid_plan_arguments_fail_before_cuda(kw):
+    args = dict(bits=8, stream_len=[4096], window_len=[1024], k=3.0, mode=0)
+    args.update(kw)
+    shape = args.pop("shape", None)
+    d = rfi.make_desc(args["bits"], args["stream_len"], args["window_len"], args["k"], args["mode"],
+                      flags=args.get("flags", 0), shape=shape)
+    st, h = rfi.rfi_plan_create(d)
+    assert st == rfi.RFI_ERR_INVALID_ARG and h is None
+
+
+def test_null_arguments():
+    assert rfi.LIB.rfi_plan_create(None, None) == rfi.RFI_ERR_INVALID_ARG
+    assert rfi.LIB.rfi_excise(None, None, None, None, None, None) == rfi.RFI_ERR_INVALID_ARG
+    assert rfi.LIB.rfi_stats(None, None, None, None, None) == rfi.RFI_ERR_INVALID_ARG
+    assert rfi.LIB.rfi_plan_get_info(None, None) == rfi.RFI_ERR_INVALID_ARG
+    assert rfi.LIB.rfi_plan_destroy(None) == rfi.RFI_OK
+
+
+def test_status_strings():
+    for s in range(9):
+        assert rfi.rfi_status_string(s) and rfi.rfi_status_string(s) != "unknown status"
+    assert rfi.rfi_status_string(99) == "unknown status"
+    assert "sm_103a" in rfi.rfi_version()

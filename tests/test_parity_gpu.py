@@ -1,0 +1,203 @@
+"""GPU path vs the CPU oracle, bit for bit, through the C ABI (small and ragged cases)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import workloads
+
+from .parity import assert_same, gen_streams, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+FORMS = {"batched": 0, "per_stream": 0x1, "graph": 0x4}
+
+
+def _run_both(rfi, xs, windows, bits, k, mode, const=0, seed=0, **kw):
+    got, st, totals, info = gpu_run(rfi, xs, windows, bits, k, mode, const, seed, **kw)
+    ref = oracle_run(xs, windows, bits, k, mode, const, seed, kw.get("stream_ids"))
+    return got, ref, st, totals, info
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+def test_single_stream_workload(cuda, rfi, form):
+    w = workloads.single()
+    xs = gen_streams(w)
+    v = w.variants[0]
+    got, ref, st, totals, info = _run_both(rfi, xs, [w.streams[0].window], 8, v.k, v.mode,
+                                           flags=FORMS[form])
+    assert st == 0
+    assert_same(got, ref, form)
+    assert totals.windows == 256 and totals.flagged == int(ref[0]["counts"].sum())
+
+
+GWB_LENS = [5 * 16384 + 1234, 3 * 16384, 2 * 16384 + 16, 777]
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+@pytest.mark.parametrize("vi", range(8))
+def test_gwb_variants_small(cuda, rfi, form, vi):
+    w = workloads.gwb60(nstreams=4)
+    v = w.variants[vi]
+    xs = gen_streams(w, GWB_LENS)
+    got, ref, st, totals, _ = _run_both(rfi, xs, [16384] * 4, 8, v.k, v.mode, v.const, v.seed,
+                                        flags=FORMS[form])
+    assert st == 0
+    assert_same(got, ref, "%s %s" % (form, v.name))
+    assert totals.flagged == sum(int(r["counts"].sum()) for r in ref)
+
+
+@pytest.mark.parametrize("form", ["batched", "per_stream"])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_twelve_bit_small(cuda, rfi, form, mode):
+    w = workloads.twelve60(nstreams=3)
+    xs = gen_streams(w, [6 * 8192 + 777, 8192, 3001])
+    got, ref, st, _, _ = _run_both(rfi, xs, [8192] * 3, 12, 3.5, mode, const=-1000, seed=7,
+                                   flags=FORMS[form])
+    assert st == 0
+    assert_same(got, ref, "12-bit mode %d" % mode)
+
+
+def test_uneven_windows_small(cuda, rfi):
+    w = workloads.uneven60(nstreams=8)
+    rng = np.random.default_rng(5)
+    wins = [1024, 2048, 4096, 8192, 16384, 32768, 65536, 1024]
+    lens = [int(W * rng.integers(1, 4) + rng.integers(0, W)) for W in wins]
+    xs = gen_streams(w, lens)
+    for flags in (0, 0x1, 0x4):
+        got, ref, st, _, _ = _run_both(rfi, xs, wins, 8, 3.0, 3, seed=7, flags=flags)
+        assert st == 0
+        assert_same(got, ref, "uneven flags %d" % flags)
+
+
+SHAPES = [
+    dict(consumer_warps=4, stages=2, ctas_per_sm=1, dynamic_tiles=1),
+    dict(consumer_warps=4, stages=4, ctas_per_sm=3, dynamic_tiles=2),
+    dict(consumer_warps=8, stages=1, ctas_per_sm=2, dynamic_tiles=1),
+    dict(consumer_warps=8, stages=3, ctas_per_sm=2, dynamic_tiles=2, stage_bytes=65536),
+    dict(consumer_warps=16, stages=2, ctas_per_sm=1, dynamic_tiles=1),
+    dict(consumer_warps=16, stages=6, ctas_per_sm=1, dynamic_tiles=2, stage_bytes=32768),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "cw%d-st%d-c%d-d%d" % (
+    s["consumer_warps"], s["stages"], s["ctas_per_sm"], s["dynamic_tiles"]))
+def test_launch_shapes(cuda, rfi, shape):
+    w = workloads.gwb60(nstreams=4)
+    xs = gen_streams(w, GWB_LENS)
+    got, ref, st, _, info = _run_both(rfi, xs, [16384] * 4, 8, 3.0, 3, seed=7, shape=shape)
+    assert st == 0 and info.shape.consumer_warps == shape["consumer_warps"]
+    assert_same(got, ref, str(shape))
+
+
+@pytest.mark.parametrize("hc", [1, 2, 4])
+def test_twelve_bit_histogram_copies(cuda, rfi, hc):
+    w = workloads.twelve60(nstreams=2)
+    xs = gen_streams(w, [3 * 8192 + 5, 8192 * 2])
+    got, ref, st, _, info = _run_both(rfi, xs, [8192] * 2, 12, 3.5, 3, seed=7,
+                                      shape=dict(hist_copies=hc, consumer_warps=8))
+    assert st == 0 and info.shape.hist_copies == hc
+    assert_same(got, ref, "hc %d" % hc)
+
+
+@pytest.mark.parametrize("W", [1, 2, 7, 16, 33, 40, 48, 100, 1000, 65536])
+@pytest.mark.parametrize("form", ["batched", "per_stream"])
+def test_odd_window_lengths(cuda, rfi, W, form):
+    p = synth.params(seed=21, sigma=16.0, burst_rate=2e-2, burst_len_max=64, bits=8)
+    n = 3 * W + (W // 3) + 1 if W > 1 else 50
+    xs = [synth.fill(p, 0, n), synth.fill(p, 1, W)]
+    for mode in (0, 2, 3):
+        got, ref, st, _, _ = _run_both(rfi, xs, [W, W], 8, 3.0, mode, seed=3, flags=FORMS[form])
+        assert st == 0
+        assert_same(got, ref, "W %d mode %d" % (W, mode))
+
+
+@pytest.mark.parametrize("bits", [8, 12])
+@pytest.mark.parametrize("offset,in_place", [(0, True), (1, False), (2, False), (8, True), (4, False)])
+def test_misaligned_and_in_place_buffers(cuda, rfi, bits, offset, in_place):
+    if bits == 12 and offset % 2:
+        pytest.skip("int16 buffers are 2-byte aligned")
+    p = synth.params(seed=22, sigma=16.0 if bits == 8 else 120.0, burst_rate=1e-2, burst_len_max=64, bits=bits)
+    xs = [synth.fill(p, s, 4 * 4096 + 99) for s in range(3)]
+    for flags in (0, 1):
+        got, ref, st, _, _ = _run_both(rfi, xs, [4096] * 3, bits, 3.0, 3, seed=9, flags=flags,
+                                       offset=offset, in_place=in_place)
+        assert st == 0
+        assert_same(got, ref, "offset %d in_place %s" % (offset, in_place))
+
+
+def test_degenerate_windows(cuda, rfi):
+    W = 4096
+    a = np.zeros(W, np.int8)                         # constant: D = 0
+    b = np.full(W, 127, np.int8)                     # saturated high
+    c = np.where(np.arange(W) % 2 == 0, -128, 127).astype(np.int8)   # two-valued, saturated
+    d = np.zeros(W, np.int8)
+    d[: W // 2 + 1] = 5                              # majority equal: D = 0 despite outliers
+    d[-10:] = -100
+    e = np.full(65536, -7, np.int8)                  # 65536 identical values: counter width
+    f = np.arange(W, dtype=np.int64).astype(np.int8)  # uniform over all 256 values
+    xs = [a, b, c, d, e, f]
+    wins = [W, W, W, W, 65536, W]
+    for mode in range(4):
+        got, ref, st, _, _ = _run_both(rfi, xs, wins, 8, 3.0, mode, const=55, seed=1)
+        assert st == 0
+        assert_same(got, ref, "degenerate mode %d" % mode)
+        assert got[0]["counts"].sum() == 0 and got[3]["mad"][0] == 0
+
+
+def test_twelve_bit_extremes_and_range_error(cuda, rfi):
+    x = np.tile(np.array([-2048, 2047, 0, 1, 2, 3, 4], np.int16), 1000)
+    got, ref, st, _, _ = _run_both(rfi, [x], [7 * 16], 12, 3.0, 2)
+    assert st == 0
+    assert_same(got, ref, "12-bit extremes")
+    bad = x.copy()
+    bad[5000] = 2048
+    got, st, totals, _ = gpu_run(rfi, [bad], [7 * 16], 12, 3.0, 2)
+    assert st == rfi.RFI_ERR_SAMPLE_RANGE and totals.device_status == rfi.RFI_ERR_SAMPLE_RANGE
+    # the next call on valid data is clean again
+    got, st, _, _ = gpu_run(rfi, [x], [7 * 16], 12, 3.0, 2)
+    assert st == 0
+
+
+def test_injected_timeout_is_reported_and_context_survives(cuda, rfi):
+    w = workloads.gwb60(nstreams=2)
+    xs = gen_streams(w, [4 * 16384, 16384 + 3])
+    got, st, totals, _ = gpu_run(rfi, xs, [16384] * 2, 8, 3.0, 0, flags=rfi.RFI_PLAN_INJECT_TIMEOUT)
+    assert st == rfi.RFI_ERR_TIMEOUT and totals.device_status == rfi.RFI_ERR_TIMEOUT
+    ref = oracle_run(xs, [16384] * 2, 8, 3.0, 0)
+    assert_same(got, ref, "after injected timeout")   # the hook delays, it does not abort
+    got, st, _, _ = gpu_run(rfi, xs, [16384] * 2, 8, 3.0, 0)
+    assert st == 0
+
+
+@pytest.mark.parametrize("bits", [8, 12])
+def test_host_pipeline(cuda, rfi, bits):
+    if bits == 8:
+        w = workloads.gwb60(nstreams=3)
+        lens, wins, k = [40 * 16384 + 321, 16384, 3000], [16384] * 3, 3.0
+    else:
+        w = workloads.twelve60(nstreams=2)
+        lens, wins, k = [2200 * 8192 + 5, 100], [8192] * 2, 3.5
+    xs = gen_streams(w, lens)
+    got, ref, st, totals, _ = _run_both(rfi, xs, wins, bits, k, 3, seed=7, host=True, calls=2)
+    assert st == 0
+    assert_same(got, ref, "host pipeline %d-bit" % bits)
+    assert totals.flagged == sum(int(r["counts"].sum()) for r in ref)
+
+
+def test_repeated_calls_and_stream_ids(cuda, rfi):
+    w = workloads.gwb60(nstreams=3)
+    xs = gen_streams(w, [3 * 16384, 2 * 16384 + 7, 16384])
+    sids = [1000, 7, 0xFFFFFFFF]
+    got, ref, st, _, _ = _run_both(rfi, xs, [16384] * 3, 8, 3.0, 3, seed=0xFEEDFACECAFEBEEF,
+                                   stream_ids=sids, calls=3)
+    assert st == 0
+    assert_same(got, ref, "repeat")
+
+
+def test_autotuned_plan(cuda, rfi):
+    w = workloads.gwb60(nstreams=4)
+    xs = gen_streams(w, GWB_LENS)
+    got, ref, st, _, info = _run_both(rfi, xs, [16384] * 4, 8, 5.0, 2, flags=rfi.RFI_PLAN_AUTOTUNE | 0x4)
+    assert st == 0 and info.grid >= 1
+    assert_same(got, ref, "autotuned")
