@@ -346,7 +346,8 @@ def run_ours(args):
                        "launch_shape": {"consumer_warps": info.shape.consumer_warps, "stages": info.shape.stages,
                                         "ctas_per_sm": info.shape.ctas_per_sm,
                                         "stage_bytes": info.shape.stage_bytes,
-                                        "dynamic_tiles": info.shape.dynamic_tiles, "grid": info.grid},
+                                        "dynamic_tiles": info.shape.dynamic_tiles, "groups": info.shape.groups,
+                                        "grid": info.grid},
                        "l2": "inputs (%d MiB per rank) larger than L2 (129 MB)" % (samples_per_call >> 20),
                        "parallelism": "replicas (one 60-stream batch per GPU)", "feed_gen_s": round(t_gen, 2)},
             "per_stream": {"value": ps_value, "unit": UNIT, "ms_per_step": ps_ms / ps_steps, "steps": ps_steps,

@@ -99,6 +99,8 @@ typedef struct rfi_launch_shape {
     int32_t stage_bytes;     /* bytes per buffer (>= the largest window); 0 = choose */
     int32_t dynamic_tiles;   /* 1: tiles taken from an atomic counter; 2: static round robin */
     int32_t hist_copies;     /* 12-bit histogram copies (1, 2, 4); ignored for 8-bit */
+    int32_t groups;          /* consumer groups per CTA, 1 or 2 (each with its own copy warp;
+                                2 needs consumer_warps <= 8) */
 } rfi_launch_shape;
 
 typedef struct rfi_plan_desc {

@@ -34,7 +34,8 @@ RFI_PLAN_INJECT_TIMEOUT = 0x100
 class RfiLaunchShape(ctypes.Structure):
     _fields_ = [("consumer_warps", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("stage_bytes", ctypes.c_int32),
-                ("dynamic_tiles", ctypes.c_int32), ("hist_copies", ctypes.c_int32)]
+                ("dynamic_tiles", ctypes.c_int32), ("hist_copies", ctypes.c_int32),
+                ("groups", ctypes.c_int32)]
 
 
 class RfiPlanDesc(ctypes.Structure):

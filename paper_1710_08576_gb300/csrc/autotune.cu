@@ -3,11 +3,15 @@
 // for 12-bit samples, histogram copies. Every candidate that fits is timed with CUDA events on a
 // scratch copy of the plan's own window layout (capped at 256 MiB of input) filled with
 // noise-like samples; the fastest shape is kept. Results are cached per process by
-// (device, sample width, mode, window layout).
+// (device, sample width, mode, window layout), and in the file named by the environment
+// variable RFI_TUNE_CACHE when it is set (one "key<TAB>shape" line per entry).
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <map>
 #include <mutex>
 #include <string>
@@ -84,6 +88,34 @@ std::string cache_key(const rfi_plan_s *P) {
     return k;
 }
 
+bool cache_file_lookup(const std::string &key, Shape *out) {
+    const char *path = std::getenv("RFI_TUNE_CACHE");
+    if (!path || !*path) return false;
+    std::ifstream f(path);
+    std::string line;
+    bool found = false;
+    while (std::getline(f, line)) {
+        const size_t tab = line.find('\t');
+        if (tab == std::string::npos || line.compare(0, tab, key) != 0 || tab != key.size()) continue;
+        std::istringstream is(line.substr(tab + 1));
+        Shape s{};
+        if (is >> s.consumer_warps >> s.stages >> s.ctas_per_sm >> s.stage_bytes >> s.dynamic_tiles >> s.hist_copies >>
+            s.groups) {
+            *out = s;
+            found = true;  // the last entry for a key wins
+        }
+    }
+    return found;
+}
+
+void cache_file_store(const std::string &key, const Shape &s) {
+    const char *path = std::getenv("RFI_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::ofstream f(path, std::ios::app);
+    f << key << '\t' << s.consumer_warps << ' ' << s.stages << ' ' << s.ctas_per_sm << ' ' << s.stage_bytes << ' '
+      << s.dynamic_tiles << ' ' << s.hist_copies << ' ' << s.groups << '\n';
+}
+
 struct Scratch {
     uint8_t *in = nullptr, *out = nullptr;
     uint32_t *mask = nullptr, *counts = nullptr;
@@ -110,8 +142,15 @@ rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req) {
     {
         std::lock_guard<std::mutex> g(g_cache_mu);
         auto it = g_cache.find(key);
-        if (it != g_cache.end()) {
-            P->shape = it->second;
+        Shape cached{};
+        bool hit = it != g_cache.end();
+        if (hit) cached = it->second;
+        else if (cache_file_lookup(key, &cached)) {
+            hit = persistent_occupancy(P->bits, P->mode, cached) >= cached.ctas_per_sm;
+            if (hit) g_cache[key] = cached;
+        }
+        if (hit) {
+            P->shape = cached;
             rfi_status rs = plan_build_tiles(P);
             return rs == RFI_OK ? plan_alloc_workspace(P) : rs;
         }
@@ -142,6 +181,7 @@ rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req) {
         return RFI_ERR_OOM;
     }
     fill_scratch<<<1024, 256>>>(sc.in, tot / bps, P->bits);
+    if (cudaStreamSynchronize(0) != cudaSuccess) return RFI_ERR_CUDA;
     std::vector<Seg> segs(P->S);
     for (int i = 0; i < P->S; ++i) {
         Seg &g = segs[i];
@@ -171,14 +211,16 @@ rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req) {
     const int min_stage = static_cast<int>((maxwb + 127) / 128 * 128);
     std::vector<Shape> cands;
     for (int cw : {4, 8, 16})
+      for (int grp : {1, 2})
         for (int ctas : {1, 2, 3, 4})
-            for (int stages : {2, 3, 4, 6})
+            for (int stages : {1, 2, 3, 4, 6})
                 for (int mult : {1, 2, 4})
                     for (int dyn : {1, 2})
                         for (int hc : {1, 2, 4}) {
                             if (P->bits == 8 && hc != 1) continue;
                             if (!uniform && dyn == 2) continue;
-                            Shape s{cw, stages, ctas, min_stage * mult, dyn, P->bits == 8 ? 1 : hc};
+                            if (grp == 2 && cw == 16) continue;
+                            Shape s{cw, stages, ctas, min_stage * mult, dyn, P->bits == 8 ? 1 : hc, grp};
                             if (req) {
                                 if (req->consumer_warps && req->consumer_warps != cw) continue;
                                 if (req->stages && req->stages != stages) continue;
@@ -186,10 +228,11 @@ rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req) {
                                 if (req->dynamic_tiles && req->dynamic_tiles != dyn) continue;
                                 if (req->hist_copies && P->bits == 12 && req->hist_copies != hc) continue;
                                 if (req->stage_bytes && req->stage_bytes != s.stage_bytes) continue;
+                                if (req->groups && req->groups != grp) continue;
                             }
                             if (s.stage_bytes > 96 * 1024 && mult > 1) continue;
-                            if ((cw + 1) * 32 * ctas > 2048) continue;
-                            if (persistent_smem_bytes(P->bits, s) * ctas > 228u * 1024u) continue;
+                            if (grp * (cw + 1) * 32 * ctas > 2048) continue;
+                            if (persistent_smem_bytes(P->bits, P->mode, s) * ctas > 228u * 1024u) continue;
                             cands.push_back(s);
                         }
     if (cands.empty()) return RFI_ERR_UNSUPPORTED;
@@ -256,6 +299,7 @@ rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req) {
     {
         std::lock_guard<std::mutex> g(g_cache_mu);
         g_cache[key] = best;
+        cache_file_store(key, best);
     }
     rfi_status rs = plan_build_tiles(P);
     return rs == RFI_OK ? plan_alloc_workspace(P) : rs;

@@ -14,10 +14,21 @@
 //                  Eq. 2 (x >= tau_U or x <= tau_L) for integer x with Kq = round(k*1.4826*2^16);
 //                  flagged samples get the replacement value, the mask bit and the count.
 //
-// 8-bit samples use a lane-striped histogram: bin v of lane l is word v*32 + l, so the 32
-// lanes of a warp always hit 32 different banks and 32 different words; warps share the table
-// through shared-memory atomics. 12-bit samples use 1, 2 or 4 plain copies of a 4096-bin
-// table selected by lane, which spreads same-bin collisions within a warp.
+// 8-bit samples use a lane-striped histogram: the count of raw byte value u (the int8 sample
+// read as unsigned) for lane l is word u*32 + l, so the 32 lanes of a warp always hit 32
+// different banks and 32 different words; warps share the table through shared-memory
+// atomics, and the reduce phase reads row u into logical bin u ^ 128 = x + 128. 12-bit
+// samples use 1, 2 or 4 plain copies of a 4096-bin table selected by lane, which spreads
+// same-bin collisions within a warp. One warp searches the cumulative counts for M and D and
+// broadcasts the threshold and replacement values through shared memory.
+//
+// The int8 replace pass works on four samples per 32-bit word: a native byte absolute
+// difference, a three-operation byte compare against t, a byte permute that replicates each
+// byte's flag bit into 0x00/0xFF, and a byte dot product that packs the flags into mask bits.
+//
+// Digital-noise replacement is compacted per warp: each round of 32 chunks writes its
+// flagged positions to a per-warp shared list, and the warp then evaluates Philox for 32
+// listed samples at a time, so no lane idles while another one runs a long noise loop.
 
 #pragma once
 
@@ -141,22 +152,40 @@ __device__ __forceinline__ int32_t noise_value(int32_t M, uint32_t sigq, uint64_
 template <int BITS>
 struct Geo {
     static constexpr int kBins = BITS == 8 ? 256 : 4096;
-    static constexpr int kOffset = BITS == 8 ? 128 : 2048;  // bin = x + kOffset
+    static constexpr int kOffset = BITS == 8 ? 128 : 2048;  // logical bin = x + kOffset
     static constexpr int kBps = BITS == 8 ? 1 : 2;          // bytes per sample
     static constexpr int kLo = BITS == 8 ? -128 : -2048;
     static constexpr int kHi = BITS == 8 ? 127 : 2047;
     static constexpr int kCumWords = kBins + kBins / 32;     // padded: index b + b/32
-    __host__ __device__ static constexpr int hist_bytes(int ncopies) {
-        return BITS == 8 ? kBins * 32 * 4 : kBins * 4 * ncopies;
+    static constexpr int kChunkSamples = 16 / kBps;          // samples per 16-byte chunk
+    // 8-bit, one consumer group: a 32 KiB table of 128-byte rows (raw byte u -> row u, lane l
+    // -> word l). 8-bit, two groups: one 64 KiB table of 256-byte rows shared by both (group g
+    // owns bytes [128g, 128g + 128) of every row). 12-bit: ncopies tables of 4096 words per group.
+    __host__ __device__ static constexpr int hist_bytes(int ncopies, int groups) {
+        return BITS == 8 ? (groups == 2 ? 65536 : 32768) : kBins * 4 * ncopies * groups;
     }
+    __host__ __device__ static constexpr int row_bytes(int groups) { return groups == 2 ? 256 : 128; }
 };
+
+// Shared-window address of the first byte of dynamic shared memory. The 8-bit histogram sits
+// there and its atomics use it as an immediate offset; kernels check it at entry.
+constexpr uint32_t kDynSmemShared = 1024;
+
+constexpr int kNoiseListPerWarp = 512;  // positions per warp per round (32 chunks x 16 samples)
 
 __device__ __forceinline__ int pad32(int b) { return b + (b >> 5); }
 
+struct RepShared {
+    int32_t M, D, t, hiv, lov;
+    uint32_t sigq, active, pad;
+    // int8 replace constants (see Rep8)
+    uint32_t mb4, tlo7, tsmall, c4, hi4, lo4, ulo7, usmall;
+    uint32_t unone, pad2[3];
+};
+
 struct Ctl {
     uint32_t warp_tot[32];
-    int32_t mb;        // median bin
-    int32_t d;         // MAD
+    RepShared rep;     // threshold and replacement values of the current window
     uint32_t count;    // flagged samples of the current window
     int32_t go;        // consumer broadcast: tile index, -1 end, -2 timeout
     uint32_t abort;    // set when any warp gave up on a bounded wait
@@ -166,11 +195,14 @@ struct Ctl {
 
 // Per-CTA view of the shared-memory regions used by window processing.
 struct Shm {
-    uint8_t *hist;     // histogram (generic pointer)
-    uint32_t hist_s;   // histogram (shared address)
-    uint32_t *cum;     // padded cumulative counts
+    uint8_t *hist;       // histogram (generic pointer; 8-bit: the 64 KiB table)
+    uint32_t hist_s;     // histogram (shared address)
+    uint32_t grp;        // 8-bit: byte offset of this group's half row (0 or 128)
+    uint32_t *cum;       // padded cumulative counts
     Ctl *ctl;
-    int ncopies;       // 12-bit only
+    uint16_t *nlist;     // noise positions, kNoiseListPerWarp per consumer warp
+    int ncopies;         // 12-bit only
+    int bar_id;          // named barrier of this consumer group
 };
 
 // One window to process.
@@ -183,120 +215,97 @@ struct Win {
     int64_t abs_idx;      // absolute stream index of sample 0
     uint32_t sid;
     bool vec;             // out is 16-byte aligned: vector stores
-    uint32_t *count_out;  // nullable
-    int32_t *med_out;     // nullable
-    int32_t *mad_out;     // nullable
 };
 
 // ------------------------------------------------------------------ phase 1: histogram
-__device__ __forceinline__ void hist8_word(uint32_t lane_base, uint32_t w) {
-    // lane_base = hist_s + 4 * lane; bin b of byte j: byte offset b * 128
-    const uint32_t wb = w ^ 0x80808080u;  // int8 -> bin index x + 128 per byte
-    red_add_shared(lane_base + ((wb << 7) & 0x7F80u), 1u);
-    red_add_shared(lane_base + ((wb >> 1) & 0x7F80u), 1u);
-    red_add_shared(lane_base + ((wb >> 9) & 0x7F80u), 1u);
-    red_add_shared(lane_base + ((wb >> 17) & 0x7F80u), 1u);
+// Shared atomic at histogram address kDynSmemShared + a.
+__device__ __forceinline__ void red_hist8(uint32_t a) {
+    asm volatile("red.shared.add.u32 [%0+1024], %1;" ::"r"(a), "r"(1u));
 }
 
-__device__ __forceinline__ uint32_t hist12_sample(uint32_t copy_base, int32_t x) {
-    const uint32_t b = static_cast<uint32_t>(x + 2048);
-    red_add_shared(copy_base + ((b & 4095u) << 2), 1u);
-    return b > 4095u ? 1u : 0u;
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
 }
 
-__device__ __forceinline__ uint32_t hist12_word(uint32_t copy_base, uint32_t w) {
-    return hist12_sample(copy_base, static_cast<int16_t>(w & 0xFFFFu)) |
-           hist12_sample(copy_base, static_cast<int16_t>(w >> 16));
+// Four int8 samples.
+// 256-byte rows: lp = 128*group + 4*lane; the table offset of raw byte u is u*256 + lp, which one
+// byte permute assembles (byte 0 from lp, byte 1 = sample byte j, bytes 2-3 zero).
+// 128-byte rows: lp = shared address of the table + 4*lane; the address is lp + u*128.
+template <int ROWB>
+__device__ __forceinline__ void hist8_word(uint32_t lp, uint32_t w) {
+    static_assert(kDynSmemShared == 1024, "immediate offset of red_hist8");
+    if (ROWB == 256) {
+        red_hist8(prmt(w, lp, 0x5504u));
+        red_hist8(prmt(w, lp, 0x5514u));
+        red_hist8(prmt(w, lp, 0x5524u));
+        red_hist8(prmt(w, lp, 0x5534u));
+    } else {
+        red_add_shared(lp + ((w & 0xFFu) << 7), 1u);
+        red_add_shared(lp + (prmt(w, 0u, 0x4441u) << 7), 1u);
+        red_add_shared(lp + (prmt(w, 0u, 0x4442u) << 7), 1u);
+        red_add_shared(lp + ((w >> 24) << 7), 1u);
+    }
 }
 
-template <int BITS, int T>
+// Two 12-bit samples in int16 halves. The bin x + 2048 of an in-range sample is its low 12 bits
+// with bit 11 flipped; a half is in range iff its bits 15..11 are all equal, which the caller
+// accumulates as (w ^ (w << 1)) & 0xF000F000.
+__device__ __forceinline__ void hist12_word(uint32_t copy_base, uint32_t w) {
+    red_add_shared(copy_base + (((w & 0xFFFu) ^ 0x800u) << 2), 1u);
+    red_add_shared(copy_base + ((((w >> 16) & 0xFFFu) ^ 0x800u) << 2), 1u);
+}
+
+__device__ __forceinline__ uint32_t range12_bits(uint32_t w) { return (w ^ (w << 1)) & 0xF000F000u; }
+
+template <int BITS, int T, int ROWB>
 __device__ __forceinline__ void phase_histogram(const Shm &sm, const Win &w, int tid) {
     const int lane = tid & 31;
     const int nbytes = w.n * Geo<BITS>::kBps;
     const int nfull = nbytes >> 4;
     const uint4 *d4 = reinterpret_cast<const uint4 *>(w.data);
     if (BITS == 8) {
-        const uint32_t lb = sm.hist_s + 4u * lane;
+        const uint32_t lb = (ROWB == 256 ? sm.grp : sm.hist_s) + 4u * lane;
         int c = tid;
         for (; c + T < nfull; c += 2 * T) {
             const uint4 a = d4[c], b = d4[c + T];
-            hist8_word(lb, a.x); hist8_word(lb, a.y); hist8_word(lb, a.z); hist8_word(lb, a.w);
-            hist8_word(lb, b.x); hist8_word(lb, b.y); hist8_word(lb, b.z); hist8_word(lb, b.w);
+            hist8_word<ROWB>(lb, a.x); hist8_word<ROWB>(lb, a.y); hist8_word<ROWB>(lb, a.z); hist8_word<ROWB>(lb, a.w);
+            hist8_word<ROWB>(lb, b.x); hist8_word<ROWB>(lb, b.y); hist8_word<ROWB>(lb, b.z); hist8_word<ROWB>(lb, b.w);
         }
         if (c < nfull) {
             const uint4 a = d4[c];
-            hist8_word(lb, a.x); hist8_word(lb, a.y); hist8_word(lb, a.z); hist8_word(lb, a.w);
+            hist8_word<ROWB>(lb, a.x); hist8_word<ROWB>(lb, a.y); hist8_word<ROWB>(lb, a.z); hist8_word<ROWB>(lb, a.w);
         }
         const int rem = nbytes & 15;
         if (tid < rem) {
-            const uint32_t b = static_cast<uint32_t>(static_cast<int8_t>(w.data[nfull * 16 + tid]) + 128);
-            red_add_shared(lb + b * 128u, 1u);
+            const uint32_t u = static_cast<uint32_t>(w.data[nfull * 16 + tid]);
+            if (ROWB == 256) red_hist8(lb + (u << 8));
+            else red_add_shared(lb + (u << 7), 1u);
         }
     } else {
         const uint32_t cb = sm.hist_s + static_cast<uint32_t>(lane & (sm.ncopies - 1)) * 16384u;
         uint32_t bad = 0;
         for (int c = tid; c < nfull; c += T) {
             const uint4 a = d4[c];
-            bad |= hist12_word(cb, a.x) | hist12_word(cb, a.y) | hist12_word(cb, a.z) | hist12_word(cb, a.w);
+            hist12_word(cb, a.x); hist12_word(cb, a.y); hist12_word(cb, a.z); hist12_word(cb, a.w);
+            bad |= range12_bits(a.x) | range12_bits(a.y) | range12_bits(a.z) | range12_bits(a.w);
         }
         const int rem = (nbytes & 15) >> 1;
         if (tid < rem) {
-            const int16_t x = reinterpret_cast<const int16_t *>(w.data)[nfull * 8 + tid];
-            bad |= hist12_sample(cb, x);
+            const uint32_t x = reinterpret_cast<const uint16_t *>(w.data)[nfull * 8 + tid];
+            red_add_shared(cb + (((x & 0xFFFu) ^ 0x800u) << 2), 1u);
+            bad |= range12_bits(x) & 0xF000u;
         }
         if (bad) atomicOr(&sm.ctl->err, 1u);
     }
 }
 
-// ------------------------------------------------------------------ phases 2-4
-template <int BITS, int T>
-__device__ __forceinline__ void phase_reduce(const Shm &sm, int tid) {
-    const int lane = tid & 31;
-    uint32_t *cum = sm.cum;
-    if (BITS == 8) {
-        // row r = bin r: 32 lane counters (128 bytes); read and clear in 8 rotated 16-byte pieces
-        for (int r = tid; r < 256; r += T) {
-            uint4 *row = reinterpret_cast<uint4 *>(sm.hist + r * 128);
-            uint32_t s = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int qq = (q + lane) & 7;
-                const uint4 v = row[qq];
-                s += v.x + v.y + v.z + v.w;
-                row[qq] = make_uint4(0u, 0u, 0u, 0u);
-            }
-            cum[pad32(r)] = s;
-        }
-    } else {
-        uint32_t *h = reinterpret_cast<uint32_t *>(sm.hist);
-        const int nc = sm.ncopies;
-        for (int b = tid; b < 4096; b += T) {
-            uint32_t s = 0;
-            for (int c = 0; c < nc; ++c) {
-                s += h[c * 4096 + b];
-                h[c * 4096 + b] = 0u;
-            }
-            cum[pad32(b)] = s;
-        }
-    }
-}
-
-template <int BITS, int T>
-__device__ __forceinline__ void phase_scan(const Shm &sm, int tid) {
-    constexpr int B = Geo<BITS>::kBins;
-    constexpr int TE = T < B ? T : B;
-    constexpr int BPT = B / TE;
+// ------------------------------------------------------------------ phases 2-3: reduce + scan
+// Block exclusive offsets of per-thread totals `run` (named barrier inside).
+template <int T>
+__device__ __forceinline__ uint32_t block_offsets(const Shm &sm, uint32_t run, int tid) {
     const int lane = tid & 31, warp = tid >> 5;
-    uint32_t *cum = sm.cum;
-    uint32_t v[BPT];
-    uint32_t run = 0;
-    if (tid < TE) {
-#pragma unroll
-        for (int i = 0; i < BPT; ++i) {
-            run += cum[pad32(tid * BPT + i)];
-            v[i] = run;
-        }
-    }
     uint32_t inc = run;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -304,16 +313,74 @@ __device__ __forceinline__ void phase_scan(const Shm &sm, int tid) {
         if (lane >= o) inc += y;
     }
     if (lane == 31) sm.ctl->warp_tot[warp] = inc;
-    named_bar(1, T);
-    uint32_t pre = 0;
-    for (int q = 0; q < warp; ++q) pre += sm.ctl->warp_tot[q];
-    const uint32_t excl = pre + inc - run;
+    named_bar(sm.bar_id, T);
+    const uint32_t pre = __reduce_add_sync(0xFFFFFFFFu, lane < warp ? sm.ctl->warp_tot[lane] : 0u);
+    return pre + inc - run;
+}
+
+// 8-bit: thread t owns logical bins [t*BPT, (t+1)*BPT); logical bin v is lane-striped row v^128.
+// Reads and clears its rows, scans, and writes the inclusive cumulative counts.
+template <int T, int ROWB>
+__device__ __forceinline__ void phase_reduce_scan8(const Shm &sm, int tid) {
+    constexpr int TE = T < 256 ? T : 256;
+    constexpr int BPT = 256 / TE;
+    const int lane = tid & 31;
+    uint32_t v[BPT];
+    uint32_t run = 0;
     if (tid < TE) {
 #pragma unroll
-        for (int i = 0; i < BPT; ++i) cum[pad32(tid * BPT + i)] = v[i] + excl;
+        for (int i = 0; i < BPT; ++i) {
+            uint4 *row = reinterpret_cast<uint4 *>(sm.hist + ((tid * BPT + i) ^ 128) * ROWB + sm.grp);
+            uint32_t s = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int qq = (q + lane) & 7;
+                const uint4 a = row[qq];
+                s += a.x + a.y + a.z + a.w;
+                row[qq] = make_uint4(0u, 0u, 0u, 0u);
+            }
+            run += s;
+            v[i] = run;
+        }
+    }
+    const uint32_t excl = block_offsets<T>(sm, run, tid);
+    if (tid < TE) {
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) sm.cum[pad32(tid * BPT + i)] = v[i] + excl;
     }
 }
 
+// 12-bit: fold the copies into padded totals (conflict-free strided pass), then scan
+// contiguous bins per thread.
+template <int T>
+__device__ __forceinline__ void phase_reduce_scan12(const Shm &sm, int tid) {
+    constexpr int B = 4096;
+    constexpr int BPT = B / T;
+    uint32_t *h = reinterpret_cast<uint32_t *>(sm.hist);
+    uint32_t *cum = sm.cum;
+    const int nc = sm.ncopies;
+    for (int b = tid; b < B; b += T) {
+        uint32_t s = 0;
+        for (int c = 0; c < nc; ++c) {
+            s += h[c * B + b];
+            h[c * B + b] = 0u;
+        }
+        cum[pad32(b)] = s;
+    }
+    named_bar(sm.bar_id, T);
+    uint32_t v[BPT];
+    uint32_t run = 0;
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        run += cum[pad32(tid * BPT + i)];
+        v[i] = run;
+    }
+    const uint32_t excl = block_offsets<T>(sm, run, tid);
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) cum[pad32(tid * BPT + i)] = v[i] + excl;
+}
+
+// ------------------------------------------------------------------ phase 4: search
 // Smallest v in [0, B) with pred(v), for a monotone pred with pred(B-1) true; one warp.
 template <int B, typename Pred>
 __device__ __forceinline__ int warp_search(int lane, Pred pred) {
@@ -328,9 +395,24 @@ __device__ __forceinline__ int warp_search(int lane, Pred pred) {
     return base + __ffs(bal) - 1;
 }
 
+struct Rep {
+    int32_t M, D;
+    int32_t t;        // min(ceil(Kq*D / 2^16), sample span + 1)
+    int32_t hiv, lov; // threshold replacement above / below (saturated)
+    uint32_t sigq;    // 97164 * D
+    bool active;      // some sample can be flagged
+};
+
+__device__ __forceinline__ int32_t sat_to(int64_t v, int32_t lo, int32_t hi) {
+    return v < lo ? lo : (v > hi ? hi : static_cast<int32_t>(v));
+}
+
+// One warp: lower median bin, then the MAD, then the threshold and replacement values, written
+// to the shared control block.
 template <int BITS>
-__device__ __forceinline__ void phase_search(const Shm &sm, int n, int lane) {
+__device__ __forceinline__ void phase_search(const Shm &sm, int n, int lane, int64_t kq, int32_t cval) {
     constexpr int B = Geo<BITS>::kBins;
+    constexpr int SPAN = Geo<BITS>::kHi - Geo<BITS>::kLo;
     const uint32_t *cum = sm.cum;
     const uint32_t half = static_cast<uint32_t>((n + 1) >> 1);
     const int mb = warp_search<B>(lane, [&](int v) { return cum[pad32(v)] >= half; });
@@ -341,155 +423,229 @@ __device__ __forceinline__ void phase_search(const Shm &sm, int n, int lane) {
         return f >= half;
     });
     if (lane == 0) {
-        sm.ctl->mb = mb;
-        sm.ctl->d = d;
-        sm.ctl->count = 0u;
+        RepShared r;
+        r.M = mb - Geo<BITS>::kOffset;
+        r.D = d;
+        const int64_t kd = kq * static_cast<int64_t>(d);
+        const int64_t t = (kd + 65535) >> 16;
+        const int64_t c = kd >> 16;
+        r.t = static_cast<int32_t>(t < SPAN + 1 ? t : SPAN + 1);
+        r.hiv = sat_to(static_cast<int64_t>(r.M) + c, Geo<BITS>::kLo, Geo<BITS>::kHi);
+        r.lov = sat_to(static_cast<int64_t>(r.M) - c, Geo<BITS>::kLo, Geo<BITS>::kHi);
+        r.sigq = 97164u * static_cast<uint32_t>(d);
+        r.active = (d > 0 && t <= SPAN) ? 1u : 0u;  // |x - M| never exceeds the sample span
+        r.pad = 0u;
+        if (BITS == 8) {
+            const uint32_t tt = static_cast<uint32_t>(r.t > 255 ? 255 : r.t);
+            const uint32_t ub = static_cast<uint32_t>(r.M + 129);  // smallest biased value above M
+            r.mb4 = static_cast<uint32_t>(r.M + 128) * 0x01010101u;
+            r.tlo7 = (tt & 0x7Fu) * 0x01010101u;
+            r.tsmall = tt < 128u ? ~0u : 0u;
+            r.c4 = (static_cast<uint32_t>(cval) & 0xFFu) * 0x01010101u;
+            r.hi4 = (static_cast<uint32_t>(r.hiv) & 0xFFu) * 0x01010101u;
+            r.lo4 = (static_cast<uint32_t>(r.lov) & 0xFFu) * 0x01010101u;
+            r.ulo7 = (ub & 0x7Fu) * 0x01010101u;
+            r.usmall = ub < 128u ? ~0u : 0u;
+            r.unone = ub > 255u ? 1u : 0u;
+        }
+        sm.ctl->rep = r;
     }
 }
 
-// ------------------------------------------------------------------ phase 5: replace
-struct Rep {
-    int32_t M, D;
-    int64_t t;        // ceil(Kq*D / 2^16)
-    int32_t hiv, lov; // threshold replacement above / below (saturated)
-    uint32_t sigq;    // 97164 * D
-    bool active;      // some sample can be flagged
-};
-
-__device__ __forceinline__ int32_t sat_to(int64_t v, int32_t lo, int32_t hi) {
-    return v < lo ? lo : (v > hi ? hi : static_cast<int32_t>(v));
-}
-
-template <int BITS>
-__device__ __forceinline__ Rep make_rep(const Ctl *ctl, int64_t kq) {
+__device__ __forceinline__ Rep load_rep(const Ctl *ctl) {
+    const RepShared s = ctl->rep;
     Rep r;
-    r.M = ctl->mb - Geo<BITS>::kOffset;
-    r.D = ctl->d;
-    const int64_t kd = kq * static_cast<int64_t>(r.D);
-    r.t = (kd + 65535) >> 16;
-    const int64_t c = kd >> 16;
-    r.hiv = sat_to(static_cast<int64_t>(r.M) + c, Geo<BITS>::kLo, Geo<BITS>::kHi);
-    r.lov = sat_to(static_cast<int64_t>(r.M) - c, Geo<BITS>::kLo, Geo<BITS>::kHi);
-    r.sigq = 97164u * static_cast<uint32_t>(r.D);
-    // |x - M| never exceeds the sample span
-    r.active = r.D > 0 && r.t <= (Geo<BITS>::kHi - Geo<BITS>::kLo);
+    r.M = s.M;
+    r.D = s.D;
+    r.t = s.t;
+    r.hiv = s.hiv;
+    r.lov = s.lov;
+    r.sigq = s.sigq;
+    r.active = s.active != 0u;
     return r;
 }
 
-// 4 int8 samples: returns the output word and sets f to 0xFF in flagged bytes.
+// ------------------------------------------------------------------ phase 5: replace
+// Bit 7 of byte j of the result is [a_j >= c_j] for unsigned bytes, given clo7 = c & 0x7F7F7F7F
+// and csmall = all ones when every c_j < 128 (zero when every c_j >= 128). The subtraction
+// cannot borrow across bytes because (a | 0x80) >= 0x80 > (c & 0x7F).
+__device__ __forceinline__ uint32_t ge_bytes_msb(uint32_t a, uint32_t clo7, uint32_t csmall) {
+    const uint32_t d = (a | 0x80808080u) - clo7;  // bit 7: low 7 bits of a >= low 7 bits of c
+    return (a & d) | ((a | d) & csmall);
+}
+
+// Per-window constants of the int8 replace pass.
+struct Rep8 {
+    uint32_t mb4;      // (M + 128) in every byte
+    uint32_t tlo7;     // t & 0x7F in every byte
+    uint32_t tsmall;   // t < 128 ? ~0 : 0
+    uint32_t c4;       // constant replacement in every byte
+    uint32_t hi4, lo4; // threshold replacement above / below in every byte
+    uint32_t ulo7;     // (M + 129) & 0x7F in every byte (x > M test)
+    uint32_t usmall;   // M + 129 < 128 ? ~0 : 0
+    uint32_t unone;    // M == 127: nothing lies above the median
+};
+
+// 4 int8 samples: returns the output word and sets f to 0xFF in flagged bytes. Noise bytes are
+// left 0 here and written by the compacted noise pass.
 template <int MODE>
-__device__ __forceinline__ uint32_t rep8_word(uint32_t w, uint32_t mb4, uint32_t t4, uint32_t c4,
-                                              uint32_t hi4, uint32_t lo4, uint32_t &f) {
-    const uint32_t wb = w ^ 0x80808080u;
-    f = __vcmpgeu4(__vabsdiffu4(wb, mb4), t4);
+__device__ __forceinline__ uint32_t rep8_word(uint32_t w, const Rep8 &k, uint32_t &f) {
+    const uint32_t wb = w ^ 0x80808080u;                  // x + 128 in every byte
+    const uint32_t ad = __vabsdiffu4(wb, k.mb4);         // |x - M|
+    f = prmt(ge_bytes_msb(ad, k.tlo7, k.tsmall), 0u, 0xBA98u);
     uint32_t rep = 0u;
-    if (MODE == 1) rep = c4;
+    if (MODE == 1) rep = k.c4;
     if (MODE == 2) {
-        const uint32_t up = __vcmpgtu4(wb, mb4);
-        rep = (hi4 & up) | (lo4 & ~up);
+        const uint32_t up = k.unone ? 0u : prmt(ge_bytes_msb(wb, k.ulo7, k.usmall), 0u, 0xBA98u);
+        rep = (k.hi4 & up) | (k.lo4 & ~up);
     }
     return (w & ~f) | (rep & f);
 }
 
-// flag bytes (0x00/0xFF) -> 4 bits, byte j -> bit j
-__device__ __forceinline__ uint32_t byte_flags_to_bits(uint32_t f) {
-    return ((f & 0x80808080u) * 0x00204081u) >> 28;
+// Mask bits of a 16-sample chunk from its four flag words (0x00/0xFF bytes), sample j -> bit j.
+__device__ __forceinline__ uint32_t chunk_bits(uint32_t f0, uint32_t f1, uint32_t f2, uint32_t f3) {
+    const uint32_t lo = __dp4a(f1 & 0x01010101u, 0x80402010u, __dp4a(f0 & 0x01010101u, 0x08040201u, 0u));
+    const uint32_t hi = __dp4a(f3 & 0x01010101u, 0x80402010u, __dp4a(f2 & 0x01010101u, 0x08040201u, 0u));
+    return lo | (hi << 8);
 }
 
-__device__ __forceinline__ uint32_t set_byte(uint32_t w, int j, uint32_t v) {
-    const int sh = j * 8;
-    return (w & ~(0xFFu << sh)) | ((v & 0xFFu) << sh);
+// Noise values for the flagged positions `bits` of chunk c of each lane: compacted through the
+// warp's shared list so that all 32 lanes evaluate Philox together. Stores go straight to the
+// output; they follow the chunk's own store in warp order (__syncwarp).
+template <int BITS>
+__device__ __forceinline__ void noise_round(const Win &w, const Rep &r, const Params &p, uint16_t *list,
+                                            int lane, int c, uint32_t bits) {
+    constexpr int CS = Geo<BITS>::kChunkSamples;
+    const uint32_t cnt = __popc(bits);
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    if (total == 0) return;
+    uint32_t off = inc - cnt;
+    uint32_t m = bits;
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1u;
+        list[off++] = static_cast<uint16_t>(c * CS + j);
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < total; i += 32) {
+        const int pos = list[i];
+        const int32_t z = noise_value(r.M, r.sigq, p.seed, w.sid, w.abs_idx + pos, Geo<BITS>::kLo, Geo<BITS>::kHi);
+        if (BITS == 8) w.out[pos] = static_cast<uint8_t>(z);
+        else reinterpret_cast<int16_t *>(w.out)[pos] = static_cast<int16_t>(z);
+    }
+    __syncwarp();
 }
 
 template <int BITS, int MODE, int T>
-__device__ __forceinline__ uint32_t phase_replace(const Win &w, const Rep &r, const Params &p, int tid) {
+__device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, const Rep &r, const Params &p,
+                                                  int tid) {
     constexpr int BPS = Geo<BITS>::kBps;
-    constexpr int LO = Geo<BITS>::kLo, HI = Geo<BITS>::kHi;
+    const int lane = tid & 31, warp = tid >> 5;
     const int nbytes = w.n * BPS;
+    const int nfull = nbytes >> 4;
     const int nchunks = (nbytes + 15) >> 4;
     const uint4 *d4 = reinterpret_cast<const uint4 *>(w.data);
+    uint16_t *list = sm.nlist + warp * kNoiseListPerWarp;
     uint32_t flagged = 0;
     if (BITS == 8) {
-        const uint32_t mb4 = static_cast<uint32_t>(r.M + 128) * 0x01010101u;
-        const uint32_t t4 = static_cast<uint32_t>(r.t > 255 ? 255 : r.t) * 0x01010101u;
-        const uint32_t c4 = (static_cast<uint32_t>(p.cval) & 0xFFu) * 0x01010101u;
-        const uint32_t hi4 = (static_cast<uint32_t>(r.hiv) & 0xFFu) * 0x01010101u;
-        const uint32_t lo4 = (static_cast<uint32_t>(r.lov) & 0xFFu) * 0x01010101u;
+        const RepShared &rs = sm.ctl->rep;
+        Rep8 k;
+        k.mb4 = rs.mb4;
+        k.tlo7 = rs.tlo7;
+        k.tsmall = rs.tsmall;
+        k.c4 = rs.c4;
+        k.hi4 = rs.hi4;
+        k.lo4 = rs.lo4;
+        k.ulo7 = rs.ulo7;
+        k.usmall = rs.usmall;
+        k.unone = rs.unone;
         uint16_t *mk = reinterpret_cast<uint16_t *>(w.mask);
-        for (int c = tid; c < nchunks; c += T) {
-            uint4 v = d4[c];
+        uint4 *o4 = reinterpret_cast<uint4 *>(w.out);
+        // warp-uniform rounds: lane handles chunk base + lane
+        for (int base = warp * 32; base < nchunks; base += T) {
+            const int c = base + lane;
             uint32_t bits = 0;
-            if (r.active) {
-                uint32_t f0, f1, f2, f3;
-                v.x = rep8_word<MODE>(v.x, mb4, t4, c4, hi4, lo4, f0);
-                v.y = rep8_word<MODE>(v.y, mb4, t4, c4, hi4, lo4, f1);
-                v.z = rep8_word<MODE>(v.z, mb4, t4, c4, hi4, lo4, f2);
-                v.w = rep8_word<MODE>(v.w, mb4, t4, c4, hi4, lo4, f3);
-                bits = byte_flags_to_bits(f0) | (byte_flags_to_bits(f1) << 4) |
-                       (byte_flags_to_bits(f2) << 8) | (byte_flags_to_bits(f3) << 12);
-            }
-            const int valid = nbytes - c * 16;  // bytes of this chunk inside the window
-            if (valid < 16) bits &= (1u << valid) - 1u;
-            if (MODE == 3) {
-                uint32_t m = bits;
-                while (m) {
-                    const int j = __ffs(m) - 1;
-                    m &= m - 1u;
-                    const uint32_t z = static_cast<uint32_t>(
-                        noise_value(r.M, r.sigq, p.seed, w.sid, w.abs_idx + c * 16 + j, LO, HI));
-                    if (j < 4) v.x = set_byte(v.x, j, z);
-                    else if (j < 8) v.y = set_byte(v.y, j - 4, z);
-                    else if (j < 12) v.z = set_byte(v.z, j - 8, z);
-                    else v.w = set_byte(v.w, j - 12, z);
+            if (c < nchunks) {
+                uint4 v = d4[c];
+                if (r.active) {
+                    uint32_t f0, f1, f2, f3;
+                    v.x = rep8_word<MODE>(v.x, k, f0);
+                    v.y = rep8_word<MODE>(v.y, k, f1);
+                    v.z = rep8_word<MODE>(v.z, k, f2);
+                    v.w = rep8_word<MODE>(v.w, k, f3);
+                    bits = chunk_bits(f0, f1, f2, f3);
                 }
+                if (c < nfull) {
+                    if (w.vec) __stcs(o4 + c, v);
+                    else {
+                        const uint32_t ww[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) w.out[c * 16 + j] = static_cast<uint8_t>(ww[j >> 2] >> ((j & 3) * 8));
+                    }
+                } else {  // ragged last chunk of the window
+                    const int valid = nbytes - c * 16;
+                    bits &= (1u << valid) - 1u;
+                    const uint32_t ww[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (j < valid) w.out[c * 16 + j] = static_cast<uint8_t>(ww[j >> 2] >> ((j & 3) * 8));
+                }
+                flagged += __popc(bits);
+                if (mk) mk[c] = static_cast<uint16_t>(bits);
             }
-            flagged += __popc(bits);
-            if (w.vec && valid >= 16) {
-                __stcs(reinterpret_cast<uint4 *>(w.out + c * 16), v);
-            } else {
-                const uint32_t ww[4] = {v.x, v.y, v.z, v.w};
-                const int lim = valid < 16 ? valid : 16;
-                for (int j = 0; j < lim; ++j) w.out[c * 16 + j] = static_cast<uint8_t>(ww[j >> 2] >> ((j & 3) * 8));
+            if (MODE == 3) {
+                __syncwarp();
+                noise_round<8>(w, r, p, list, lane, c, bits);
             }
-            if (mk) mk[c] = static_cast<uint16_t>(bits);
         }
         if (mk) {
             for (int c = nchunks + tid; c < 2 * w.mask_words; c += T) mk[c] = 0;
         }
     } else {
         uint8_t *mk = reinterpret_cast<uint8_t *>(w.mask);
-        const int64_t t = r.t;
-        for (int c = tid; c < nchunks; c += T) {
-            const uint4 v = d4[c];
-            uint32_t ww[4] = {v.x, v.y, v.z, v.w};
-            const int valid = (nbytes - c * 16) >> 1;  // samples of this chunk in the window
+        const int32_t t = r.t;
+        for (int base = warp * 32; base < nchunks; base += T) {
+            const int c = base + lane;
             uint32_t bits = 0;
+            if (c < nchunks) {
+                const uint4 v = d4[c];
+                uint32_t ww[4] = {v.x, v.y, v.z, v.w};
+                const int valid = c < nfull ? 8 : ((nbytes - c * 16) >> 1);  // samples in the window
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int32_t x = static_cast<int16_t>((ww[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu);
-                const int32_t ad = x > r.M ? x - r.M : r.M - x;
-                const bool fl = r.active && ad >= t && j < valid;
-                if (fl) {
-                    int32_t z;
-                    if (MODE == 0) z = 0;
-                    else if (MODE == 1) z = p.cval;
-                    else if (MODE == 2) z = x > r.M ? r.hiv : r.lov;
-                    else z = noise_value(r.M, r.sigq, p.seed, w.sid, w.abs_idx + c * 8 + j, LO, HI);
+                for (int j = 0; j < 8; ++j) {
                     const int sh = (j & 1) * 16;
-                    ww[j >> 1] = (ww[j >> 1] & ~(0xFFFFu << sh)) | ((static_cast<uint32_t>(z) & 0xFFFFu) << sh);
-                    bits |= 1u << j;
+                    const int32_t x = static_cast<int16_t>((ww[j >> 1] >> sh) & 0xFFFFu);
+                    const int32_t ad = x > r.M ? x - r.M : r.M - x;
+                    const bool fl = r.active && ad >= t && j < valid;
+                    if (fl) {
+                        int32_t z = 0;
+                        if (MODE == 1) z = p.cval;
+                        else if (MODE == 2) z = x > r.M ? r.hiv : r.lov;
+                        ww[j >> 1] = (ww[j >> 1] & ~(0xFFFFu << sh)) | ((static_cast<uint32_t>(z) & 0xFFFFu) << sh);
+                        bits |= 1u << j;
+                    }
                 }
+                flagged += __popc(bits);
+                if (w.vec && c < nfull) {
+                    __stcs(reinterpret_cast<uint4 *>(w.out + c * 16), make_uint4(ww[0], ww[1], ww[2], ww[3]));
+                } else {
+                    int16_t *o = reinterpret_cast<int16_t *>(w.out);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j < valid) o[c * 8 + j] = static_cast<int16_t>((ww[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu);
+                }
+                if (mk) mk[c] = static_cast<uint8_t>(bits);
             }
-            flagged += __popc(bits);
-            if (w.vec && valid >= 8) {
-                __stcs(reinterpret_cast<uint4 *>(w.out + c * 16), make_uint4(ww[0], ww[1], ww[2], ww[3]));
-            } else {
-                int16_t *o = reinterpret_cast<int16_t *>(w.out);
-                const int lim = valid < 8 ? valid : 8;
-                for (int j = 0; j < lim; ++j)
-                    o[c * 8 + j] = static_cast<int16_t>((ww[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu);
+            if (MODE == 3) {
+                __syncwarp();
+                noise_round<12>(w, r, p, list, lane, c, bits);
             }
-            if (mk) mk[c] = static_cast<uint8_t>(bits);
         }
         if (mk) {
             for (int c = nchunks + tid; c < 4 * w.mask_words; c += T) mk[c] = 0;
@@ -500,28 +656,30 @@ __device__ __forceinline__ uint32_t phase_replace(const Win &w, const Rep &r, co
 
 // ------------------------------------------------------------------ one window
 // All T threads of the group call this; the histogram must be zero on entry and is zero again
-// on exit. Uses named barrier 1 over T threads.
-template <int BITS, int MODE, int T>
-__device__ void process_window(const Shm &sm, const Win &w, const Params &p, int tid) {
-    const int lane = tid & 31, warp = tid >> 5;
-    phase_histogram<BITS, T>(sm, w, tid);
-    named_bar(1, T);
-    phase_reduce<BITS, T>(sm, tid);
-    named_bar(1, T);
-    phase_scan<BITS, T>(sm, tid);
-    named_bar(1, T);
-    if (warp == 0) phase_search<BITS>(sm, w.n, lane);
-    named_bar(1, T);
-    const Rep r = make_rep<BITS>(sm.ctl, p.kq);
-    uint32_t f = phase_replace<BITS, MODE, T>(w, r, p, tid);
+// on exit. Uses the group's named barrier (five times per window for 8-bit samples). Thread 0
+// of the group writes the window's count, median and MAD to slot `widx` of the segment.
+template <int BITS, int MODE, int T, int ROWB>
+__device__ void process_window(const Shm &sm, const Win &w, const Seg &sg, int64_t widx, const Params &p,
+                               int tid) {
+    const int lane = tid & 31;
+    phase_histogram<BITS, T, ROWB>(sm, w, tid);
+    named_bar(sm.bar_id, T);
+    if (BITS == 8) phase_reduce_scan8<T, ROWB>(sm, tid);
+    else phase_reduce_scan12<T>(sm, tid);
+    named_bar(sm.bar_id, T);
+    if (tid < 32) phase_search<BITS>(sm, w.n, lane, p.kq, p.cval);
+    named_bar(sm.bar_id, T);
+    const Rep r = load_rep(sm.ctl);
+    uint32_t f = phase_replace<BITS, MODE, T>(sm, w, r, p, tid);
     f = __reduce_add_sync(0xFFFFFFFFu, f);
     if (lane == 0 && f) atomicAdd(&sm.ctl->count, f);
-    named_bar(1, T);
+    named_bar(sm.bar_id, T);
     if (tid == 0) {
         const uint32_t cnt = sm.ctl->count;
-        if (w.count_out) *w.count_out = cnt;
-        if (w.med_out) *w.med_out = r.M;
-        if (w.mad_out) *w.mad_out = r.D;
+        sm.ctl->count = 0u;
+        if (sg.counts) sg.counts[widx] = cnt;
+        if (sg.med) sg.med[widx] = r.M;
+        if (sg.mad) sg.mad[widx] = r.D;
         sm.ctl->flagged += cnt;
         if (BITS == 12 && sm.ctl->err) {
             atomicOr(p.status, kStatusSampleRange);

@@ -9,6 +9,7 @@ namespace rfi {
 // Bits that kernels OR into the plan's device status word.
 constexpr uint32_t kStatusSampleRange = 1u;  // reported as RFI_ERR_SAMPLE_RANGE
 constexpr uint32_t kStatusTimeout = 2u;      // reported as RFI_ERR_TIMEOUT
+constexpr uint32_t kStatusLayout = 4u;       // unexpected shared-memory window: RFI_ERR_UNSUPPORTED
 
 // One contiguous run of windows of one stream, starting on a window boundary.
 struct Seg {
@@ -51,11 +52,12 @@ struct Shape {
     int stage_bytes;      // multiple of 128, >= the largest tile
     int dynamic_tiles;    // 1: atomic counter, 2: static round robin
     int hist_copies;      // 12-bit histogram copies
+    int groups;           // consumer groups per CTA (1 or 2)
 };
 
 // Bytes of dynamic shared memory the kernels need.
-size_t persistent_smem_bytes(int bits, const Shape &s);
-size_t stream_smem_bytes(int bits, int consumer_warps, int ncopies, int window_bytes);
+size_t persistent_smem_bytes(int bits, int mode, const Shape &s);
+size_t stream_smem_bytes(int bits, int mode, int consumer_warps, int ncopies, int window_bytes);
 
 // Maximum resident CTAs per SM of the persistent kernel for this shape (0 if it cannot run).
 int persistent_occupancy(int bits, int mode, const Shape &s);

@@ -12,14 +12,16 @@ int persistent_occupancy_b12(int, const Shape &);
 cudaError_t launch_stream_b8(int, int, const Seg &, int64_t, int64_t, const Params &, cudaStream_t);
 cudaError_t launch_stream_b12(int, int, const Seg &, int64_t, int64_t, const Params &, cudaStream_t);
 
-size_t persistent_smem_bytes(int bits, const Shape &s) {
-    return bits == 8 ? dev::layout<8>(s.hist_copies, s.stages, s.stage_bytes).total
-                     : dev::layout<12>(s.hist_copies, s.stages, s.stage_bytes).total;
+size_t persistent_smem_bytes(int bits, int mode, const Shape &s) {
+    return bits == 8
+               ? dev::layout<8>(s.hist_copies, s.stages, s.stage_bytes, s.consumer_warps, s.groups, mode).total
+               : dev::layout<12>(s.hist_copies, s.stages, s.stage_bytes, s.consumer_warps, s.groups, mode).total;
 }
 
-size_t stream_smem_bytes(int bits, int, int ncopies, int window_bytes) {
+size_t stream_smem_bytes(int bits, int mode, int consumer_warps, int ncopies, int window_bytes) {
     const int wb = dev::align_up(window_bytes, 128);
-    return bits == 8 ? dev::layout<8>(ncopies, 1, wb).total : dev::layout<12>(ncopies, 1, wb).total;
+    return bits == 8 ? dev::layout<8>(ncopies, 1, wb, consumer_warps, 1, mode).total
+                     : dev::layout<12>(ncopies, 1, wb, consumer_warps, 1, mode).total;
 }
 
 int persistent_occupancy(int bits, int mode, const Shape &s) {

@@ -5,13 +5,13 @@ namespace rfi {
 
 cudaError_t launch_persistent_b12(int mode, const Shape &s, int grid, const Seg *segs, const Tile *tiles,
                                   int ntiles, const Params &p, unsigned *counter, int inject, cudaStream_t st) {
-    RFI_DISPATCH_MODE_CW(12, dev::persistent_launch_t, mode, s.consumer_warps, s, grid, segs, tiles, ntiles, p,
-                         counter, inject, st);
+    RFI_DISPATCH_PERSISTENT(12, dev::persistent_launch_t, mode, s.consumer_warps, s.groups, s, grid, segs, tiles,
+                            ntiles, p, counter, inject, st);
     return cudaErrorInvalidValue;
 }
 
 int persistent_occupancy_b12(int mode, const Shape &s) {
-    RFI_DISPATCH_MODE_CW(12, dev::persistent_occ_t, mode, s.consumer_warps, s);
+    RFI_DISPATCH_PERSISTENT(12, dev::persistent_occ_t, mode, s.consumer_warps, s.groups, s);
     return 0;
 }
 

@@ -15,30 +15,60 @@ constexpr uint64_t kInjectTimeoutNs = 1000000ull;    // 1 ms for the test hook
 
 __host__ __device__ constexpr int align_up(int v, int a) { return (v + a - 1) / a * a; }
 
-struct Layout {
-    int hist, cum, ctl, bar, meta, stage, total;
+// Per-stage descriptor written by the copy warp: the tile, its segment and the tile index.
+struct StageMeta {
+    Tile tile;
+    Seg seg;
+    int32_t tidx;   // tile index, -1: no more tiles
+    int32_t pad[3];
 };
 
+// Dynamic shared memory: the histogram at offset 0 (8-bit: one 64 KiB table for all groups;
+// 12-bit: per group), then one block per consumer group (cumulative counts, control block,
+// noise lists, mbarriers, stage descriptors), then the stage buffers of every group.
+struct Layout {
+    int grp;        // first group block
+    int grp_size;   // bytes per group block
+    int cum, ctl, nlist, bar, meta;  // offsets inside a group block
+    int stage;      // first stage buffer; group g stage s at stage + (g * stages + s) * stage_bytes
+    int total;
+};
+
+// The noise lists exist only for digital-noise replacement (mode 3).
 template <int BITS>
-__host__ __device__ inline Layout layout(int ncopies, int stages, int stage_bytes) {
+__host__ __device__ inline Layout layout(int ncopies, int stages, int stage_bytes, int cw, int groups, int mode) {
     Layout L;
-    L.hist = 0;
-    L.cum = align_up(Geo<BITS>::hist_bytes(ncopies), 128);
-    L.ctl = align_up(L.cum + Geo<BITS>::kCumWords * 4, 128);
-    L.bar = align_up(L.ctl + static_cast<int>(sizeof(Ctl)), 128);
-    L.meta = L.bar + (2 * kMaxStages + 1) * 8;
-    L.stage = align_up(L.meta + kMaxStages * 4, 128);
-    L.total = L.stage + stages * stage_bytes;
+    L.grp = align_up(Geo<BITS>::hist_bytes(ncopies, groups), 128);
+    L.cum = 0;
+    L.ctl = align_up(Geo<BITS>::kCumWords * 4, 128);
+    L.nlist = align_up(L.ctl + static_cast<int>(sizeof(Ctl)), 128);
+    L.bar = align_up(L.nlist + (mode == 3 ? cw * kNoiseListPerWarp * 2 : 0), 128);
+    L.meta = align_up(L.bar + (2 * kMaxStages + 1) * 8, 128);
+    L.grp_size = align_up(L.meta + kMaxStages * static_cast<int>(sizeof(StageMeta)), 128);
+    L.stage = L.grp + groups * L.grp_size;
+    L.total = L.stage + groups * stages * stage_bytes;
     return L;
 }
 
+// The shared-memory view of consumer group g.
 template <int BITS>
-__device__ __forceinline__ void zero_shared_state(const Shm &sm, int tid, int nthreads) {
-    uint4 *h = reinterpret_cast<uint4 *>(sm.hist);
-    const int n16 = Geo<BITS>::hist_bytes(sm.ncopies) / 16;
-    for (int i = tid; i < n16; i += nthreads) h[i] = make_uint4(0u, 0u, 0u, 0u);
-    uint32_t *c = reinterpret_cast<uint32_t *>(sm.ctl);
-    for (int i = tid; i < static_cast<int>(sizeof(Ctl) / 4); i += nthreads) c[i] = 0u;
+__device__ __forceinline__ Shm group_view(uint8_t *smem, const Layout &L, int g, int ncopies) {
+    Shm sm;
+    uint8_t *gb = smem + L.grp + g * L.grp_size;
+    sm.hist = BITS == 8 ? smem : smem + g * Geo<12>::kBins * 4 * ncopies;  // 8-bit: one table
+    sm.hist_s = smem_addr(sm.hist);
+    sm.grp = BITS == 8 ? 128u * static_cast<uint32_t>(g) : 0u;
+    sm.cum = reinterpret_cast<uint32_t *>(gb + L.cum);
+    sm.ctl = reinterpret_cast<Ctl *>(gb + L.ctl);
+    sm.nlist = reinterpret_cast<uint16_t *>(gb + L.nlist);
+    sm.ncopies = ncopies;
+    sm.bar_id = 1 + g;
+    return sm;
+}
+
+__device__ __forceinline__ void zero_shared(uint8_t *smem, int bytes, int tid, int nthreads) {
+    uint4 *h = reinterpret_cast<uint4 *>(smem);
+    for (int i = tid; i < bytes / 16; i += nthreads) h[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 __device__ __forceinline__ Win make_win(const Seg &sg, int64_t w, const uint8_t *data, int bps) {
@@ -53,37 +83,42 @@ __device__ __forceinline__ Win make_win(const Seg &sg, int64_t w, const uint8_t 
     win.abs_idx = sg.abs0 + s0;
     win.sid = sg.stream_id;
     win.vec = sg.vec != 0;
-    win.count_out = sg.counts ? sg.counts + w : nullptr;
-    win.med_out = sg.med ? sg.med + w : nullptr;
-    win.mad_out = sg.mad ? sg.mad + w : nullptr;
     return win;
 }
 
 // ------------------------------------------------------------------ persistent kernel
-// Warps 0..CW-1 process windows; warp CW is the copy warp. Stage s of the shared ring holds one
-// tile; full[s] completes when its bytes have landed (bulk copy + transaction count), empty[s]
-// when the consumers are done with it. All waits are bounded.
-template <int BITS, int MODE, int CW>
-__global__ void __launch_bounds__((CW + 1) * 32)
+// G consumer groups per CTA, each with CW consumer warps and one copy warp. The copy warp of a
+// group owns a ring of `stages` shared-memory buffers; for each tile it fills the stage
+// descriptor, arms the stage's full barrier with the byte count and issues one bulk copy.
+// The group's consumers wait on the full barrier, process the tile's windows, and release the
+// stage through its empty barrier. All waits are bounded.
+template <int BITS, int MODE, int CW, int G>
+__global__ void __launch_bounds__(G *(CW + 1) * 32)
 persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, int ntiles, Params p,
                   int stages, int stage_bytes, int dynamic_tiles, unsigned *counter, int inject_timeout) {
-    constexpr int T = CW * 32;
+    constexpr int T = CW * 32;          // consumer threads per group
+    constexpr int GT = (CW + 1) * 32;   // threads per group
     constexpr int BPS = Geo<BITS>::kBps;
     extern __shared__ __align__(128) uint8_t smem[];
-    const Layout L = layout<BITS>(p.ncopies, stages, stage_bytes);
-    Shm sm;
-    sm.hist = smem + L.hist;
-    sm.hist_s = smem_addr(sm.hist);
-    sm.cum = reinterpret_cast<uint32_t *>(smem + L.cum);
-    sm.ctl = reinterpret_cast<Ctl *>(smem + L.ctl);
-    sm.ncopies = p.ncopies;
-    const uint32_t bar0 = smem_addr(smem + L.bar);
+    if (BITS == 8 && smem_addr(smem) != kDynSmemShared) {
+        if (threadIdx.x == 0) atomicOr(p.status, kStatusLayout);
+        return;
+    }
+    const Layout L = layout<BITS>(p.ncopies, stages, stage_bytes, CW, G, MODE);
+    const int g = threadIdx.x / GT;
+    const int tid = threadIdx.x % GT;
+    const int warp = tid >> 5, lane = tid & 31;
+    const Shm sm = group_view<BITS>(smem, L, g, p.ncopies);
+    uint8_t *gb = smem + L.grp + g * L.grp_size;
+    const uint32_t bar0 = smem_addr(gb + L.bar);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (kMaxStages + s); };
     const uint32_t inj_bar = bar0 + 8u * (2 * kMaxStages);
-    int *meta = reinterpret_cast<int *>(smem + L.meta);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    StageMeta *meta = reinterpret_cast<StageMeta *>(gb + L.meta);
+    uint8_t *stage0 = smem + L.stage + g * stages * stage_bytes;
 
+    zero_shared(smem, L.stage, threadIdx.x, blockDim.x);  // histogram and group blocks
+    __syncthreads();
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(full_bar(s), 1);
@@ -92,9 +127,10 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
         mbar_init(inj_bar, 1);
         fence_mbar_init();
     }
-    zero_shared_state<BITS>(sm, tid, blockDim.x);
     __syncthreads();
 
+    const unsigned qid = blockIdx.x * G + g;  // static tile queue of this group
+    const unsigned nq = gridDim.x * G;
     if (warp == CW) {
         // ---------------- copy warp
         int issued = 0;  // iterations whose full barrier was armed
@@ -117,32 +153,33 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
             int t = 0;
             if (lane == 0)
                 t = dynamic_tiles == 1 ? static_cast<int>(atomicAdd(counter, 1u))
-                                       : static_cast<int>(blockIdx.x + static_cast<unsigned>(it) * gridDim.x);
+                                       : static_cast<int>(qid + static_cast<unsigned>(it) * nq);
             t = __shfl_sync(0xFFFFFFFFu, t, 0);
             issued = it + 1;
             if (t >= ntiles) {
                 if (lane == 0) {
-                    meta[s] = -1;
+                    meta[s].tidx = -1;
                     mbar_arrive(full_bar(s));
                 }
                 break;
             }
             const Tile tl = tiles[t];
             const Seg &sg = segs[tl.seg];
-            uint8_t *stage = smem + L.stage + s * stage_bytes;
-            if (sg.vec) {
-                const uint8_t *src = sg.in + static_cast<int64_t>(tl.w0) * sg.W * BPS;
-                const uint32_t bulk = tl.bytes & ~15u, rem = tl.bytes & 15u;
-                if (static_cast<uint32_t>(lane) < rem) stage[bulk + lane] = src[bulk + lane];
-                __syncwarp();
-                if (lane == 0) {
-                    meta[s] = t;
-                    mbar_arrive_tx(full_bar(s), bulk);
-                    if (bulk) bulk_g2s(smem_addr(stage), src, bulk, full_bar(s));
-                }
-            } else if (lane == 0) {
-                meta[s] = t;
-                mbar_arrive(full_bar(s));
+            // the stage descriptor: lanes 0..3 copy the tile, lanes 4..23 the segment
+            static_assert(sizeof(Tile) == 16 && sizeof(Seg) == 80, "descriptor copy layout");
+            uint32_t *md = reinterpret_cast<uint32_t *>(&meta[s]);
+            if (lane < 4) md[lane] = reinterpret_cast<const uint32_t *>(tiles + t)[lane];
+            else if (lane < 24) md[lane] = reinterpret_cast<const uint32_t *>(segs + tl.seg)[lane - 4];
+            uint8_t *stage = stage0 + s * stage_bytes;
+            const bool vec = sg.vec != 0;
+            const uint8_t *src = sg.in + static_cast<int64_t>(tl.w0) * sg.W * BPS;
+            const uint32_t bulk = vec ? (tl.bytes & ~15u) : 0u, rem = tl.bytes & 15u;
+            if (vec && static_cast<uint32_t>(lane) < rem) stage[bulk + lane] = src[bulk + lane];
+            __syncwarp();
+            if (lane == 0) {
+                meta[s].tidx = t;
+                mbar_arrive_tx(full_bar(s), bulk);
+                if (bulk) bulk_g2s(smem_addr(stage), src, bulk, full_bar(s));
             }
         }
         // drain: every armed stage has landed before the copy warp leaves
@@ -153,8 +190,8 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
         return;
     }
 
-    // ---------------- consumer warps
-    if (inject_timeout && blockIdx.x == 0 && tid == 0) {
+    // ---------------- consumer warps of group g
+    if (inject_timeout && blockIdx.x == 0 && g == 0 && tid == 0) {
         if (!mbar_wait_bounded(inj_bar, 0, kInjectTimeoutNs)) atomicOr(p.status, kStatusTimeout);
     }
     for (int it = 0;; ++it) {
@@ -162,28 +199,29 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
         const int u = it / stages;
         if (tid == 0) {
             const bool ok = mbar_wait_bounded(full_bar(s), u & 1, kWaitTimeoutNs);
-            sm.ctl->go = ok ? meta[s] : -2;
+            sm.ctl->go = ok ? meta[s].tidx : -2;
             if (!ok) {
                 atomicOr(p.status, kStatusTimeout);
                 atomicExch(&sm.ctl->abort, 1u);
             }
         }
-        named_bar(1, T);
+        named_bar(sm.bar_id, T);
         const int t = *reinterpret_cast<volatile int *>(&sm.ctl->go);
         if (t == -2) break;
         mbar_try_wait(full_bar(s), u & 1);  // phase is complete: acquire for this thread
         if (t < 0) break;
-        const Tile tl = tiles[t];
-        const Seg &sg = segs[tl.seg];
-        uint8_t *stage = smem + L.stage + s * stage_bytes;
+        const Tile tl = meta[s].tile;
+        const Seg &sg = meta[s].seg;
+        uint8_t *stage = stage0 + s * stage_bytes;
         if (!sg.vec) {
             const uint8_t *src = sg.in + static_cast<int64_t>(tl.w0) * sg.W * BPS;
             for (int i = tid; i < static_cast<int>(tl.bytes); i += T) stage[i] = src[i];
-            named_bar(1, T);
+            named_bar(sm.bar_id, T);
         }
         for (uint32_t k = 0; k < tl.nw; ++k) {
-            const Win win = make_win(sg, static_cast<int64_t>(tl.w0) + k, stage + k * sg.W * BPS, BPS);
-            process_window<BITS, MODE, T>(sm, win, p, tid);
+            const int64_t widx = static_cast<int64_t>(tl.w0) + k;
+            const Win win = make_win(sg, widx, stage + k * sg.W * BPS, BPS);
+            process_window<BITS, MODE, T, Geo<BITS>::row_bytes(G)>(sm, win, sg, widx, p, tid);
         }
         if (tid == 0) mbar_arrive(empty_bar(s));
     }
@@ -196,16 +234,15 @@ __global__ void __launch_bounds__(CW * 32) stream_kernel(Seg sg, int64_t w_begin
     constexpr int T = CW * 32;
     constexpr int BPS = Geo<BITS>::kBps;
     extern __shared__ __align__(128) uint8_t smem[];
-    const Layout L = layout<BITS>(p.ncopies, 1, 0);
-    Shm sm;
-    sm.hist = smem + L.hist;
-    sm.hist_s = smem_addr(sm.hist);
-    sm.cum = reinterpret_cast<uint32_t *>(smem + L.cum);
-    sm.ctl = reinterpret_cast<Ctl *>(smem + L.ctl);
-    sm.ncopies = p.ncopies;
+    if (BITS == 8 && smem_addr(smem) != kDynSmemShared) {
+        if (threadIdx.x == 0) atomicOr(p.status, kStatusLayout);
+        return;
+    }
+    const Layout L = layout<BITS>(p.ncopies, 1, 0, CW, 1, MODE);
+    const Shm sm = group_view<BITS>(smem, L, 0, p.ncopies);
     const int tid = threadIdx.x;
     uint8_t *buf = smem + L.stage;
-    zero_shared_state<BITS>(sm, tid, T);
+    zero_shared(smem, L.stage, tid, T);
     const int64_t w = w_begin + blockIdx.x;
     const int64_t s0 = w * sg.W;
     const int n = static_cast<int>(sg.len - s0 < sg.W ? sg.len - s0 : sg.W);
@@ -222,14 +259,14 @@ __global__ void __launch_bounds__(CW * 32) stream_kernel(Seg sg, int64_t w_begin
     }
     __syncthreads();
     const Win win = make_win(sg, w, buf, BPS);
-    process_window<BITS, MODE, T>(sm, win, p, tid);
+    process_window<BITS, MODE, T, Geo<BITS>::row_bytes(1)>(sm, win, sg, w, p, tid);
     if (tid == 0 && sm.ctl->flagged) atomicAdd(p.flagged, sm.ctl->flagged);
 }
 
 // ------------------------------------------------------------------ host-side dispatch
 // Raise the dynamic shared-memory cap of one kernel instantiation, once per process. The tag
 // parameters make the static once-flag distinct for every instantiation.
-template <int KIND, int BITS, int MODE, int CW, typename K>
+template <int KIND, int BITS, int MODE, int CW, int G, typename K>
 inline cudaError_t allow_smem(K kernel) {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
@@ -239,40 +276,58 @@ inline cudaError_t allow_smem(K kernel) {
     return err;
 }
 
-template <int BITS, int MODE, int CW>
+template <int BITS, int MODE, int CW, int G>
 cudaError_t persistent_launch_t(const Shape &s, int grid, const Seg *segs, const Tile *tiles, int ntiles,
                                 const Params &p, unsigned *counter, int inject, cudaStream_t st) {
-    auto k = persistent_kernel<BITS, MODE, CW>;
-    cudaError_t e = allow_smem<0, BITS, MODE, CW>(k);
+    auto k = persistent_kernel<BITS, MODE, CW, G>;
+    cudaError_t e = allow_smem<0, BITS, MODE, CW, G>(k);
     if (e != cudaSuccess) return e;
-    const Layout L = layout<BITS>(p.ncopies, s.stages, s.stage_bytes);
-    k<<<grid, (CW + 1) * 32, L.total, st>>>(segs, tiles, ntiles, p, s.stages, s.stage_bytes, s.dynamic_tiles,
-                                            counter, inject);
+    const Layout L = layout<BITS>(p.ncopies, s.stages, s.stage_bytes, CW, G, MODE);
+    k<<<grid, G * (CW + 1) * 32, L.total, st>>>(segs, tiles, ntiles, p, s.stages, s.stage_bytes, s.dynamic_tiles,
+                                                counter, inject);
     return cudaGetLastError();
 }
 
-template <int BITS, int MODE, int CW>
+template <int BITS, int MODE, int CW, int G>
 int persistent_occ_t(const Shape &s) {
-    auto k = persistent_kernel<BITS, MODE, CW>;
-    if (allow_smem<0, BITS, MODE, CW>(k) != cudaSuccess) return 0;
-    const Layout L = layout<BITS>(s.hist_copies, s.stages, s.stage_bytes);
+    auto k = persistent_kernel<BITS, MODE, CW, G>;
+    if (allow_smem<0, BITS, MODE, CW, G>(k) != cudaSuccess) return 0;
+    const Layout L = layout<BITS>(s.hist_copies, s.stages, s.stage_bytes, CW, G, MODE);
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, (CW + 1) * 32, L.total) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, G * (CW + 1) * 32, L.total) != cudaSuccess) return 0;
     return n;
 }
 
 template <int BITS, int MODE, int CW>
 cudaError_t stream_launch_t(const Seg &sg, int64_t w_begin, int64_t nw, const Params &p, cudaStream_t st) {
     auto k = stream_kernel<BITS, MODE, CW>;
-    cudaError_t e = allow_smem<1, BITS, MODE, CW>(k);
+    cudaError_t e = allow_smem<1, BITS, MODE, CW, 1>(k);
     if (e != cudaSuccess) return e;
-    const Layout L = layout<BITS>(p.ncopies, 1, align_up(sg.W * Geo<BITS>::kBps, 128));
+    const Layout L = layout<BITS>(p.ncopies, 1, align_up(sg.W * Geo<BITS>::kBps, 128), CW, 1, MODE);
     for (int64_t b = 0; b < nw; b += 0x7FFFFFFF) {
-        const int64_t g = nw - b < 0x7FFFFFFF ? nw - b : 0x7FFFFFFF;
-        k<<<static_cast<unsigned>(g), CW * 32, L.total, st>>>(sg, w_begin + b, p);
+        const int64_t gsz = nw - b < 0x7FFFFFFF ? nw - b : 0x7FFFFFFF;
+        k<<<static_cast<unsigned>(gsz), CW * 32, L.total, st>>>(sg, w_begin + b, p);
     }
     return cudaGetLastError();
 }
+
+// Template dispatch over (mode, consumer warps[, groups]).
+#define RFI_CASE_MCG(BITS, FN, M, C, G, ...) \
+    case (M * 1000 + C * 10 + G): return FN<BITS, M, C, G>(__VA_ARGS__);
+#define RFI_CASES_CG(BITS, FN, M, ...)                                                       \
+    RFI_CASE_MCG(BITS, FN, M, 4, 1, __VA_ARGS__) RFI_CASE_MCG(BITS, FN, M, 8, 1, __VA_ARGS__)  \
+    RFI_CASE_MCG(BITS, FN, M, 16, 1, __VA_ARGS__) RFI_CASE_MCG(BITS, FN, M, 4, 2, __VA_ARGS__) \
+    RFI_CASE_MCG(BITS, FN, M, 8, 2, __VA_ARGS__)
+#define RFI_DISPATCH_PERSISTENT(BITS, FN, MODE, CW, G, ...)        \
+    do {                                                           \
+        switch (MODE * 1000 + CW * 10 + G) {                       \
+            RFI_CASES_CG(BITS, FN, 0, __VA_ARGS__)                 \
+            RFI_CASES_CG(BITS, FN, 1, __VA_ARGS__)                 \
+            RFI_CASES_CG(BITS, FN, 2, __VA_ARGS__)                 \
+            RFI_CASES_CG(BITS, FN, 3, __VA_ARGS__)                 \
+            default: break;                                        \
+        }                                                          \
+    } while (0)
 
 #define RFI_DISPATCH_MODE_CW(BITS, FN, MODE, CW, ...)                                          \
     do {                                                                                       \

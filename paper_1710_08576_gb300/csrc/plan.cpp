@@ -32,7 +32,8 @@ bool valid_shape(const rfi_launch_shape &s) {
     return s.consumer_warps >= 0 && s.stages >= 0 && s.stages <= 8 && s.ctas_per_sm >= 0 &&
            s.ctas_per_sm <= 4 && s.stage_bytes >= 0 && s.stage_bytes <= 227 * 1024 && s.dynamic_tiles >= 0 &&
            s.dynamic_tiles <= 2 && s.hist_copies >= 0 && s.hist_copies <= 4 && s.hist_copies != 3 &&
-           (s.consumer_warps == 0 || s.consumer_warps == 4 || s.consumer_warps == 8 || s.consumer_warps == 16);
+           (s.consumer_warps == 0 || s.consumer_warps == 4 || s.consumer_warps == 8 || s.consumer_warps == 16) &&
+           s.groups >= 0 && s.groups <= 2 && !(s.groups == 2 && s.consumer_warps == 16);
 }
 
 }  // namespace
@@ -51,16 +52,17 @@ rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req) {
     }
     const int min_stage = static_cast<int>((maxwb + 127) / 128 * 128);
     s.consumer_warps = (req && req->consumer_warps) ? req->consumer_warps : 8;
+    s.groups = (req && req->groups) ? req->groups : (s.consumer_warps <= 8 ? 2 : 1);
     s.stage_bytes = std::max(min_stage, (req && req->stage_bytes) ? req->stage_bytes : 16384);
     s.stage_bytes = (s.stage_bytes + 127) / 128 * 128;
-    s.stages = (req && req->stages) ? req->stages : std::max(2, std::min(6, 65536 / s.stage_bytes));
+    s.stages = (req && req->stages) ? req->stages : std::max(2, std::min(4, 65536 / s.stage_bytes));
     s.hist_copies = P->bits == 8 ? 1 : ((req && req->hist_copies) ? req->hist_copies : 2);
     s.dynamic_tiles = (req && req->dynamic_tiles) ? req->dynamic_tiles : (uniform ? 2 : 1);
-    const int want_ctas = (req && req->ctas_per_sm) ? req->ctas_per_sm : 2;
-    if (persistent_smem_bytes(P->bits, s) > 227u * 1024u) {
+    const int want_ctas = (req && req->ctas_per_sm) ? req->ctas_per_sm : (s.groups == 2 ? 1 : 2);
+    if (persistent_smem_bytes(P->bits, P->mode, s) > 227u * 1024u) {
         if (req && req->stages) return RFI_ERR_UNSUPPORTED;
-        while (s.stages > 1 && persistent_smem_bytes(P->bits, s) > 227u * 1024u) --s.stages;
-        if (persistent_smem_bytes(P->bits, s) > 227u * 1024u) return RFI_ERR_UNSUPPORTED;
+        while (s.stages > 1 && persistent_smem_bytes(P->bits, P->mode, s) > 227u * 1024u) --s.stages;
+        if (persistent_smem_bytes(P->bits, P->mode, s) > 227u * 1024u) return RFI_ERR_UNSUPPORTED;
     }
     const int occ = persistent_occupancy(P->bits, P->mode, s);
     if (occ < 1) return cudaGetLastError() != cudaSuccess ? RFI_ERR_CUDA : RFI_ERR_UNSUPPORTED;
@@ -344,7 +346,8 @@ rfi_status rfi_stats(rfi_plan_t P, int32_t *const *median, int32_t *const *mad, 
     DevCounters h;
     RFI_CUDA(cudaMemcpyAsync(&h, P->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
     RFI_CUDA(cudaStreamSynchronize(st));
-    const rfi_status dev = (h.status & kStatusTimeout) ? RFI_ERR_TIMEOUT
+    const rfi_status dev = (h.status & kStatusTimeout)       ? RFI_ERR_TIMEOUT
+                           : (h.status & kStatusLayout)      ? RFI_ERR_UNSUPPORTED
                            : (h.status & kStatusSampleRange) ? RFI_ERR_SAMPLE_RANGE
                                                              : RFI_OK;
     if (totals) {
@@ -370,6 +373,7 @@ rfi_status rfi_plan_get_info(rfi_plan_t P, rfi_plan_info *info) {
     info->shape.stage_bytes = P->shape.stage_bytes;
     info->shape.dynamic_tiles = P->shape.dynamic_tiles;
     info->shape.hist_copies = P->shape.hist_copies;
+    info->shape.groups = P->shape.groups;
     info->sm_count = P->sm_count;
     info->kernels_per_call = (P->flags & RFI_PLAN_PER_STREAM) ? P->S : 1;
     return RFI_OK;

@@ -71,17 +71,20 @@ def test_uneven_windows_small(cuda, rfi):
 
 
 SHAPES = [
-    dict(consumer_warps=4, stages=2, ctas_per_sm=1, dynamic_tiles=1),
-    dict(consumer_warps=4, stages=4, ctas_per_sm=3, dynamic_tiles=2),
-    dict(consumer_warps=8, stages=1, ctas_per_sm=2, dynamic_tiles=1),
-    dict(consumer_warps=8, stages=3, ctas_per_sm=2, dynamic_tiles=2, stage_bytes=65536),
-    dict(consumer_warps=16, stages=2, ctas_per_sm=1, dynamic_tiles=1),
-    dict(consumer_warps=16, stages=6, ctas_per_sm=1, dynamic_tiles=2, stage_bytes=32768),
+    dict(consumer_warps=4, stages=2, ctas_per_sm=1, dynamic_tiles=1, groups=1),
+    dict(consumer_warps=4, stages=4, ctas_per_sm=2, dynamic_tiles=2, groups=1),
+    dict(consumer_warps=8, stages=1, ctas_per_sm=2, dynamic_tiles=1, groups=1),
+    dict(consumer_warps=8, stages=2, ctas_per_sm=1, dynamic_tiles=2, stage_bytes=65536, groups=1),
+    dict(consumer_warps=16, stages=2, ctas_per_sm=1, dynamic_tiles=1, groups=1),
+    dict(consumer_warps=16, stages=4, ctas_per_sm=1, dynamic_tiles=2, stage_bytes=32768, groups=1),
+    dict(consumer_warps=4, stages=3, ctas_per_sm=1, dynamic_tiles=1, groups=2),
+    dict(consumer_warps=8, stages=4, ctas_per_sm=1, dynamic_tiles=2, groups=2),
+    dict(consumer_warps=8, stages=1, ctas_per_sm=1, dynamic_tiles=1, groups=2, stage_bytes=32768),
 ]
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "cw%d-st%d-c%d-d%d" % (
-    s["consumer_warps"], s["stages"], s["ctas_per_sm"], s["dynamic_tiles"]))
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "cw%d-st%d-c%d-d%d-g%d" % (
+    s["consumer_warps"], s["stages"], s["ctas_per_sm"], s["dynamic_tiles"], s["groups"]))
 def test_launch_shapes(cuda, rfi, shape):
     w = workloads.gwb60(nstreams=4)
     xs = gen_streams(w, GWB_LENS)
@@ -90,13 +93,15 @@ def test_launch_shapes(cuda, rfi, shape):
     assert_same(got, ref, str(shape))
 
 
+@pytest.mark.parametrize("groups", [1, 2])
 @pytest.mark.parametrize("hc", [1, 2, 4])
-def test_twelve_bit_histogram_copies(cuda, rfi, hc):
+def test_twelve_bit_histogram_copies(cuda, rfi, hc, groups):
     w = workloads.twelve60(nstreams=2)
     xs = gen_streams(w, [3 * 8192 + 5, 8192 * 2])
     got, ref, st, _, info = _run_both(rfi, xs, [8192] * 2, 12, 3.5, 3, seed=7,
-                                      shape=dict(hist_copies=hc, consumer_warps=8))
-    assert st == 0 and info.shape.hist_copies == hc
+                                      shape=dict(hist_copies=hc, consumer_warps=8, groups=groups,
+                                                 stages=1 if hc * groups == 8 else 2))
+    assert st == 0 and info.shape.hist_copies == hc and info.shape.groups == groups
     assert_same(got, ref, "hc %d" % hc)
 
 
