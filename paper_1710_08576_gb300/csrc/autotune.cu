@@ -248,6 +248,7 @@ rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req) {
     p.cval = P->cval;
     p.status = &sc.ctr->status;
     p.flagged = &sc.ctr->flagged;
+    set_round_keys(p);
     Shape best{};
     float best_ms = 1e30f;
     std::vector<Tile> cur;

@@ -53,6 +53,18 @@ __device__ __forceinline__ void named_bar(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Named barrier that also returns whether any participating thread passed v = true.
+__device__ __forceinline__ bool named_bar_or(int id, int nthreads, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(v)), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
@@ -90,14 +102,27 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
     return t;
 }
 
+// try_wait that lets the hardware suspend the thread for up to ~2 us while the phase is open,
+// so a waiting warp does not take issue slots from the warps doing work.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(2000u)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase of the given parity, giving up after timeout_ns of wall time (and after
 // a fixed number of polls in any case). Returns false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t timeout_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
-    for (uint32_t it = 1; it < (1u << 26); ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 31u) == 0 && global_timer_ns() - t0 > timeout_ns) return false;
+    for (uint32_t it = 1; it < (1u << 24); ++it) {
+        if (mbar_try_wait_sleep(bar, parity)) return true;
+        if ((it & 7u) == 0 && global_timer_ns() - t0 > timeout_ns) return false;
     }
     return false;
 }
@@ -114,16 +139,14 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 // ------------------------------------------------------------------ Philox4x32-10 noise
 // Philox4x32-10 as defined by Salmon, Moraes, Dror and Shaw (SC'11): ten rounds; in each the
 // words 0 and 2 are multiplied by the two round multipliers, the high product halves are
-// xor-ed with words 1 and 3 and with the round key, and the key advances by two Weyl
-// increments between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+// xor-ed with words 1 and 3 and with the round key. The round keys (the key advanced by two
+// Weyl increments per round) come precomputed in rk0 / rk1.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t *rk0, const uint32_t *rk1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
         const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        c = make_uint4(hi1 ^ c.y ^ rk0[r], lo1, hi0 ^ c.w ^ rk1[r], lo0);
     }
     return c;
 }
@@ -132,14 +155,15 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // S2 = 2 * (sum of the eight 16-bit halves of the Philox output) - 8 * 65535.
 // |S2| <= 524280 and sigq < 2^29, so |S2| * sigq < 2^48; dividing by 2^16 first and then by
 // 107020 equals one floor division by their product.
-__device__ __forceinline__ int32_t noise_value(int32_t M, uint32_t sigq, uint64_t seed, uint32_t sid,
+__device__ __forceinline__ int32_t noise_value(int32_t M, uint32_t sigq, const Params &p, uint32_t sid,
                                                int64_t idx, int32_t lo, int32_t hi) {
     const uint4 r = philox4x32_10(
         make_uint4(static_cast<uint32_t>(idx), static_cast<uint32_t>(static_cast<uint64_t>(idx) >> 32),
                    sid, 0u),
-        static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
-    const uint32_t s = (r.x & 0xFFFFu) + (r.x >> 16) + (r.y & 0xFFFFu) + (r.y >> 16) + (r.z & 0xFFFFu) +
-                       (r.z >> 16) + (r.w & 0xFFFFu) + (r.w >> 16);
+        p.rk0, p.rk1);
+    // sum of the eight 16-bit halves: each dp2a adds both halves of one word (weights 1, 1)
+    const uint32_t s = __dp2a_lo(r.x, 0x0101u, __dp2a_lo(r.y, 0x0101u, __dp2a_lo(r.z, 0x0101u,
+                                                                              __dp2a_lo(r.w, 0x0101u, 0u))));
     const int32_t S2 = 2 * static_cast<int32_t>(s) - 8 * 65535;
     const uint32_t mag_s2 = static_cast<uint32_t>(S2 < 0 ? -S2 : S2);
     const uint64_t a = static_cast<uint64_t>(mag_s2) * sigq + 3506831360ull;  // + 107020 * 2^15
@@ -175,7 +199,7 @@ constexpr int kNoiseListPerWarp = 512;  // positions per warp per round (32 chun
 
 __device__ __forceinline__ int pad32(int b) { return b + (b >> 5); }
 
-struct RepShared {
+struct __align__(16) RepShared {
     int32_t M, D, t, hiv, lov;
     uint32_t sigq, active, pad;
     // int8 replace constants (see Rep8)
@@ -185,12 +209,19 @@ struct RepShared {
 
 struct Ctl {
     uint32_t warp_tot[32];
-    RepShared rep;     // threshold and replacement values of the current window
-    uint32_t count;    // flagged samples of the current window
-    int32_t go;        // consumer broadcast: tile index, -1 end, -2 timeout
-    uint32_t abort;    // set when any warp gave up on a bounded wait
-    uint32_t err;      // 12-bit range error seen in the current window
-    unsigned long long flagged;  // CTA total
+    RepShared rep;       // threshold and replacement values of the current window
+    uint32_t count[2];   // flagged samples, by window parity
+    uint32_t done[2];    // warps finished with the window, by window parity
+    uint32_t err[2];     // 12-bit range error seen in the window, by window parity
+    uint32_t abort;      // set when any warp gave up on a bounded wait
+    int32_t mb;          // median bin of the current window (written by its owner thread)
+    unsigned long long flagged;  // group total
+};
+
+// Per-thread running row sums of the 8-bit histogram (the table is never cleared: a window's
+// count of a bin is the difference of two consecutive sums, exact modulo 2^32).
+struct RowSums {
+    uint32_t s[2];
 };
 
 // Per-CTA view of the shared-memory regions used by window processing.
@@ -260,7 +291,7 @@ __device__ __forceinline__ void hist12_word(uint32_t copy_base, uint32_t w) {
 __device__ __forceinline__ uint32_t range12_bits(uint32_t w) { return (w ^ (w << 1)) & 0xF000F000u; }
 
 template <int BITS, int T, int ROWB>
-__device__ __forceinline__ void phase_histogram(const Shm &sm, const Win &w, int tid) {
+__device__ __forceinline__ void phase_histogram(const Shm &sm, const Win &w, int tid, int par) {
     const int lane = tid & 31;
     const int nbytes = w.n * Geo<BITS>::kBps;
     const int nfull = nbytes >> 4;
@@ -297,7 +328,7 @@ __device__ __forceinline__ void phase_histogram(const Shm &sm, const Win &w, int
             red_add_shared(cb + (((x & 0xFFFu) ^ 0x800u) << 2), 1u);
             bad |= range12_bits(x) & 0xF000u;
         }
-        if (bad) atomicOr(&sm.ctl->err, 1u);
+        if (bad) atomicOr(&sm.ctl->err[par], 1u);
     }
 }
 
@@ -319,41 +350,49 @@ __device__ __forceinline__ uint32_t block_offsets(const Shm &sm, uint32_t run, i
 }
 
 // 8-bit: thread t owns logical bins [t*BPT, (t+1)*BPT); logical bin v is lane-striped row v^128.
-// Reads and clears its rows, scans, and writes the inclusive cumulative counts.
+// Sums its rows (the difference from the previous sum is this window's count), scans, writes
+// the inclusive cumulative counts, and the thread whose bin holds the ceil(n/2)-th sample
+// records it as the median bin.
 template <int T, int ROWB>
-__device__ __forceinline__ void phase_reduce_scan8(const Shm &sm, int tid) {
+__device__ __forceinline__ void phase_reduce_scan8(const Shm &sm, int tid, RowSums &rs, int n) {
     constexpr int TE = T < 256 ? T : 256;
     constexpr int BPT = 256 / TE;
+    static_assert(BPT <= 2, "RowSums holds two rows");
     const int lane = tid & 31;
-    uint32_t v[BPT];
+    uint32_t v[BPT], h[BPT];
     uint32_t run = 0;
     if (tid < TE) {
 #pragma unroll
         for (int i = 0; i < BPT; ++i) {
-            uint4 *row = reinterpret_cast<uint4 *>(sm.hist + ((tid * BPT + i) ^ 128) * ROWB + sm.grp);
+            const uint4 *row = reinterpret_cast<const uint4 *>(sm.hist + ((tid * BPT + i) ^ 128) * ROWB + sm.grp);
             uint32_t s = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const int qq = (q + lane) & 7;
-                const uint4 a = row[qq];
+                const uint4 a = row[(q + lane) & 7];
                 s += a.x + a.y + a.z + a.w;
-                row[qq] = make_uint4(0u, 0u, 0u, 0u);
             }
-            run += s;
+            h[i] = s - rs.s[i];
+            rs.s[i] = s;
+            run += h[i];
             v[i] = run;
         }
     }
     const uint32_t excl = block_offsets<T>(sm, run, tid);
     if (tid < TE) {
+        const uint32_t half = static_cast<uint32_t>((n + 1) >> 1);
 #pragma unroll
-        for (int i = 0; i < BPT; ++i) sm.cum[pad32(tid * BPT + i)] = v[i] + excl;
+        for (int i = 0; i < BPT; ++i) {
+            const uint32_t c = v[i] + excl;
+            sm.cum[pad32(tid * BPT + i)] = c;
+            if (c >= half && c - h[i] < half) sm.ctl->mb = tid * BPT + i;
+        }
     }
 }
 
 // 12-bit: fold the copies into padded totals (conflict-free strided pass), then scan
 // contiguous bins per thread.
 template <int T>
-__device__ __forceinline__ void phase_reduce_scan12(const Shm &sm, int tid) {
+__device__ __forceinline__ void phase_reduce_scan12(const Shm &sm, int tid, int n) {
     constexpr int B = 4096;
     constexpr int BPT = B / T;
     uint32_t *h = reinterpret_cast<uint32_t *>(sm.hist);
@@ -376,8 +415,15 @@ __device__ __forceinline__ void phase_reduce_scan12(const Shm &sm, int tid) {
         v[i] = run;
     }
     const uint32_t excl = block_offsets<T>(sm, run, tid);
+    const uint32_t half = static_cast<uint32_t>((n + 1) >> 1);
+    uint32_t prev = excl;
 #pragma unroll
-    for (int i = 0; i < BPT; ++i) cum[pad32(tid * BPT + i)] = v[i] + excl;
+    for (int i = 0; i < BPT; ++i) {
+        const uint32_t c = v[i] + excl;
+        cum[pad32(tid * BPT + i)] = c;
+        if (c >= half && prev < half) sm.ctl->mb = tid * BPT + i;
+        prev = c;
+    }
 }
 
 // ------------------------------------------------------------------ phase 4: search
@@ -415,7 +461,7 @@ __device__ __forceinline__ void phase_search(const Shm &sm, int n, int lane, int
     constexpr int SPAN = Geo<BITS>::kHi - Geo<BITS>::kLo;
     const uint32_t *cum = sm.cum;
     const uint32_t half = static_cast<uint32_t>((n + 1) >> 1);
-    const int mb = warp_search<B>(lane, [&](int v) { return cum[pad32(v)] >= half; });
+    const int mb = sm.ctl->mb;  // found by its owner thread during the scan
     const int d = warp_search<B>(lane, [&](int dd) {
         const int hi = mb + dd < B - 1 ? mb + dd : B - 1;
         const int lo = mb - dd - 1;
@@ -503,10 +549,14 @@ __device__ __forceinline__ uint32_t rep8_word(uint32_t w, const Rep8 &k, uint32_
 }
 
 // Mask bits of a 16-sample chunk from its four flag words (0x00/0xFF bytes), sample j -> bit j.
+// A flag byte read as signed is -1, so a signed byte dot product with negated powers of two
+// (-1, -2, -4, -8 for the first word of a half, -16 .. -128 for the second) packs 8 flags.
 __device__ __forceinline__ uint32_t chunk_bits(uint32_t f0, uint32_t f1, uint32_t f2, uint32_t f3) {
-    const uint32_t lo = __dp4a(f1 & 0x01010101u, 0x80402010u, __dp4a(f0 & 0x01010101u, 0x08040201u, 0u));
-    const uint32_t hi = __dp4a(f3 & 0x01010101u, 0x80402010u, __dp4a(f2 & 0x01010101u, 0x08040201u, 0u));
-    return lo | (hi << 8);
+    const int lo = __dp4a(static_cast<int>(f1), static_cast<int>(0x80C0E0F0u),
+                          __dp4a(static_cast<int>(f0), static_cast<int>(0xF8FCFEFFu), 0));
+    const int hi = __dp4a(static_cast<int>(f3), static_cast<int>(0x80C0E0F0u),
+                          __dp4a(static_cast<int>(f2), static_cast<int>(0xF8FCFEFFu), 0));
+    return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 8);
 }
 
 // Noise values for the flagged positions `bits` of chunk c of each lane: compacted through the
@@ -535,7 +585,7 @@ __device__ __forceinline__ void noise_round(const Win &w, const Rep &r, const Pa
     __syncwarp();
     for (uint32_t i = lane; i < total; i += 32) {
         const int pos = list[i];
-        const int32_t z = noise_value(r.M, r.sigq, p.seed, w.sid, w.abs_idx + pos, Geo<BITS>::kLo, Geo<BITS>::kHi);
+        const int32_t z = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pos, Geo<BITS>::kLo, Geo<BITS>::kHi);
         if (BITS == 8) w.out[pos] = static_cast<uint8_t>(z);
         else reinterpret_cast<int16_t *>(w.out)[pos] = static_cast<int16_t>(z);
     }
@@ -554,21 +604,43 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
     uint16_t *list = sm.nlist + warp * kNoiseListPerWarp;
     uint32_t flagged = 0;
     if (BITS == 8) {
-        const RepShared &rs = sm.ctl->rep;
+        const uint4 *rq = reinterpret_cast<const uint4 *>(&sm.ctl->rep);
+        const uint4 q2 = rq[2], q3 = rq[3], q4 = rq[4];
         Rep8 k;
-        k.mb4 = rs.mb4;
-        k.tlo7 = rs.tlo7;
-        k.tsmall = rs.tsmall;
-        k.c4 = rs.c4;
-        k.hi4 = rs.hi4;
-        k.lo4 = rs.lo4;
-        k.ulo7 = rs.ulo7;
-        k.usmall = rs.usmall;
-        k.unone = rs.unone;
+        k.mb4 = q2.x;
+        k.tlo7 = q2.y;
+        k.tsmall = q2.z;
+        k.c4 = q2.w;
+        k.hi4 = q3.x;
+        k.lo4 = q3.y;
+        k.ulo7 = q3.z;
+        k.usmall = q3.w;
+        k.unone = q4.x;
         uint16_t *mk = reinterpret_cast<uint16_t *>(w.mask);
         uint4 *o4 = reinterpret_cast<uint4 *>(w.out);
+        int base = warp * 32;
+        if (r.active && w.vec && mk) {
+            // rounds in which all 32 chunks of the warp are full: no bounds checks
+            for (; base + 32 <= nfull; base += T) {
+                const int c = base + lane;
+                uint4 v = d4[c];
+                uint32_t f0, f1, f2, f3;
+                v.x = rep8_word<MODE>(v.x, k, f0);
+                v.y = rep8_word<MODE>(v.y, k, f1);
+                v.z = rep8_word<MODE>(v.z, k, f2);
+                v.w = rep8_word<MODE>(v.w, k, f3);
+                const uint32_t bits = chunk_bits(f0, f1, f2, f3);
+                __stcs(o4 + c, v);
+                mk[c] = static_cast<uint16_t>(bits);
+                flagged += __popc(bits);
+                if (MODE == 3) {
+                    __syncwarp();
+                    noise_round<8>(w, r, p, list, lane, c, bits);
+                }
+            }
+        }
         // warp-uniform rounds: lane handles chunk base + lane
-        for (int base = warp * 32; base < nchunks; base += T) {
+        for (; base < nchunks; base += T) {
             const int c = base + lane;
             uint32_t bits = 0;
             if (c < nchunks) {
@@ -656,36 +728,45 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
 
 // ------------------------------------------------------------------ one window
 // All T threads of the group call this; the histogram must be zero on entry and is zero again
-// on exit. Uses the group's named barrier (five times per window for 8-bit samples). Thread 0
-// of the group writes the window's count, median and MAD to slot `widx` of the segment.
+// when the first warp leaves the reduce phase. Uses the group's named barrier three times
+// (after the histogram, inside the scan, after the cumulative counts) plus once after the
+// search. There is no barrier at the end: each warp adds its flag count and marks itself done,
+// and the last warp of the window (window parity `par`) writes the count, median and MAD to
+// slot `widx` of the segment and, when release_bar != 0, releases the stage through it.
+// `stage_ok` is this thread's result of waiting for the stage (false: timed out); the first
+// barrier combines it, and the function returns false if any thread of the group timed out.
 template <int BITS, int MODE, int T, int ROWB>
-__device__ void process_window(const Shm &sm, const Win &w, const Seg &sg, int64_t widx, const Params &p,
-                               int tid) {
+__device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64_t widx, const Params &p,
+                               int tid, int par, uint32_t release_bar, bool stage_ok, RowSums &rs) {
+    constexpr int NW = T / 32;
     const int lane = tid & 31;
-    phase_histogram<BITS, T, ROWB>(sm, w, tid);
-    named_bar(sm.bar_id, T);
-    if (BITS == 8) phase_reduce_scan8<T, ROWB>(sm, tid);
-    else phase_reduce_scan12<T>(sm, tid);
+    if (stage_ok) phase_histogram<BITS, T, ROWB>(sm, w, tid, par);
+    if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
+    if (BITS == 8) phase_reduce_scan8<T, ROWB>(sm, tid, rs, w.n);
+    else phase_reduce_scan12<T>(sm, tid, w.n);
     named_bar(sm.bar_id, T);
     if (tid < 32) phase_search<BITS>(sm, w.n, lane, p.kq, p.cval);
     named_bar(sm.bar_id, T);
     const Rep r = load_rep(sm.ctl);
     uint32_t f = phase_replace<BITS, MODE, T>(sm, w, r, p, tid);
     f = __reduce_add_sync(0xFFFFFFFFu, f);
-    if (lane == 0 && f) atomicAdd(&sm.ctl->count, f);
-    named_bar(sm.bar_id, T);
-    if (tid == 0) {
-        const uint32_t cnt = sm.ctl->count;
-        sm.ctl->count = 0u;
-        if (sg.counts) sg.counts[widx] = cnt;
-        if (sg.med) sg.med[widx] = r.M;
-        if (sg.mad) sg.mad[widx] = r.D;
-        sm.ctl->flagged += cnt;
-        if (BITS == 12 && sm.ctl->err) {
-            atomicOr(p.status, kStatusSampleRange);
-            sm.ctl->err = 0u;
+    if (lane == 0) {
+        if (f) atomicAdd(&sm.ctl->count[par], f);
+        __threadfence_block();
+        if (atomicAdd(&sm.ctl->done[par], 1u) == NW - 1) {
+            // last warp of this window: every count is in and every read of the stage is done
+            __threadfence_block();
+            const uint32_t cnt = atomicExch(&sm.ctl->count[par], 0u);
+            sm.ctl->done[par] = 0u;
+            if (sg.counts) sg.counts[widx] = cnt;
+            if (sg.med) sg.med[widx] = r.M;
+            if (sg.mad) sg.mad[widx] = r.D;
+            sm.ctl->flagged += cnt;
+            if (BITS == 12 && atomicExch(&sm.ctl->err[par], 0u)) atomicOr(p.status, kStatusSampleRange);
+            if (release_bar) mbar_arrive(release_bar);
         }
     }
+    return true;
 }
 
 }  // namespace dev

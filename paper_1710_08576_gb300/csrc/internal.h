@@ -43,7 +43,20 @@ struct Params {
     int32_t ncopies;              // 12-bit histogram copies (1, 2 or 4)
     uint32_t *status;             // device status word (atomicOr of kStatus*)
     unsigned long long *flagged;  // device total of flagged samples
+    uint32_t rk0[10], rk1[10];    // Philox4x32-10 round keys of `seed` (see set_round_keys)
 };
+
+// Philox4x32-10 key schedule: round r uses (seed_lo + r * 0x9E3779B9, seed_hi + r * 0xBB67AE85)
+// (the Weyl increments of Salmon et al., SC'11), precomputed so kernels read them as constants.
+inline void set_round_keys(Params &p) {
+    uint32_t k0 = static_cast<uint32_t>(p.seed), k1 = static_cast<uint32_t>(p.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        p.rk0[r] = k0;
+        p.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
 
 struct Shape {
     int consumer_warps;   // 4, 8 or 16

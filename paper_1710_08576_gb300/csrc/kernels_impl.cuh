@@ -194,37 +194,51 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
     if (inject_timeout && blockIdx.x == 0 && g == 0 && tid == 0) {
         if (!mbar_wait_bounded(inj_bar, 0, kInjectTimeoutNs)) atomicOr(p.status, kStatusTimeout);
     }
+    int par = 0;  // window parity
+    bool timed_out = false;
+    RowSums rs = {{0u, 0u}};
     for (int it = 0;; ++it) {
         const int s = it % stages;
         const int u = it / stages;
-        if (tid == 0) {
-            const bool ok = mbar_wait_bounded(full_bar(s), u & 1, kWaitTimeoutNs);
-            sm.ctl->go = ok ? meta[s].tidx : -2;
-            if (!ok) {
-                atomicOr(p.status, kStatusTimeout);
-                atomicExch(&sm.ctl->abort, 1u);
-            }
+        // every consumer thread waits for the stage itself (bounded). The first named barrier
+        // after the wait is always a bar.red.or, so a thread that timed out and the others
+        // agree on leaving.
+        const bool ok = mbar_wait_bounded(full_bar(s), u & 1, kWaitTimeoutNs);
+        const int t = ok ? meta[s].tidx : -2;
+        if (t < 0) {  // end of the work list (-1, seen alike by every thread) or a timeout (-2)
+            timed_out = named_bar_or(sm.bar_id, T, t == -2);
+            break;
         }
-        named_bar(sm.bar_id, T);
-        const int t = *reinterpret_cast<volatile int *>(&sm.ctl->go);
-        if (t == -2) break;
-        mbar_try_wait(full_bar(s), u & 1);  // phase is complete: acquire for this thread
-        if (t < 0) break;
         const Tile tl = meta[s].tile;
         const Seg &sg = meta[s].seg;
         uint8_t *stage = stage0 + s * stage_bytes;
         if (!sg.vec) {
             const uint8_t *src = sg.in + static_cast<int64_t>(tl.w0) * sg.W * BPS;
             for (int i = tid; i < static_cast<int>(tl.bytes); i += T) stage[i] = src[i];
-            named_bar(sm.bar_id, T);
+            if (named_bar_or(sm.bar_id, T, false)) {
+                timed_out = true;
+                break;
+            }
         }
-        for (uint32_t k = 0; k < tl.nw; ++k) {
+        bool alive = true;
+        for (uint32_t k = 0; k < tl.nw && alive; ++k) {
             const int64_t widx = static_cast<int64_t>(tl.w0) + k;
             const Win win = make_win(sg, widx, stage + k * sg.W * BPS, BPS);
-            process_window<BITS, MODE, T, Geo<BITS>::row_bytes(G)>(sm, win, sg, widx, p, tid);
+            alive = process_window<BITS, MODE, T, Geo<BITS>::row_bytes(G)>(
+                sm, win, sg, widx, p, tid, par, k + 1 == tl.nw ? empty_bar(s) : 0u, true, rs);
+            par ^= 1;
         }
-        if (tid == 0) mbar_arrive(empty_bar(s));
+        if (!alive) {
+            timed_out = true;
+            break;
+        }
     }
+    if (timed_out && tid == 0) {
+        atomicOr(p.status, kStatusTimeout);
+        atomicExch(&sm.ctl->abort, 1u);
+    }
+    // the group's flagged total, once every warp of the group has finished
+    named_bar(sm.bar_id, T);
     if (tid == 0 && sm.ctl->flagged) atomicAdd(p.flagged, sm.ctl->flagged);
 }
 
@@ -259,7 +273,9 @@ __global__ void __launch_bounds__(CW * 32) stream_kernel(Seg sg, int64_t w_begin
     }
     __syncthreads();
     const Win win = make_win(sg, w, buf, BPS);
-    process_window<BITS, MODE, T, Geo<BITS>::row_bytes(1)>(sm, win, sg, w, p, tid);
+    RowSums rs = {{0u, 0u}};
+    process_window<BITS, MODE, T, Geo<BITS>::row_bytes(1)>(sm, win, sg, w, p, tid, 0, 0u, true, rs);
+    __syncthreads();
     if (tid == 0 && sm.ctl->flagged) atomicAdd(p.flagged, sm.ctl->flagged);
 }
 

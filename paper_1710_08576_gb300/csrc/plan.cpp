@@ -134,6 +134,7 @@ Params plan_params(const rfi_plan_s *P) {
     p.ncopies = P->shape.hist_copies;
     p.status = &P->d_ctr->status;
     p.flagged = &P->d_ctr->flagged;
+    set_round_keys(p);
     return p;
 }
 
