@@ -168,6 +168,35 @@ RFI_API rfi_status rfi_plan_get_info(rfi_plan_t plan, rfi_plan_info *info);
 /* Release the plan and everything it owns. NULL-safe; safe after a device error. */
 RFI_API rfi_status rfi_plan_destroy(rfi_plan_t plan);
 
+/* Allocation-free excision. The paper has no counterpart: this entry point exists for callers
+ * that must not allocate device memory while they excise, such as a real-time receiver loop
+ * whose device memory is set aside once at start-up (an allocation can synchronise the device
+ * and stall the sample stream) or a host whose memory budget is owned by another allocator.
+ *
+ * Same computation and layouts as rfi_plan_create + rfi_excise + rfi_stats with the batched
+ * form, but with no plan: desc describes the call (flags 0 or RFI_PLAN_BATCHED; desc->shape is
+ * ignored, a fixed launch shape is used), and the persistent kernel's work list, segment table
+ * and counters live in one fixed device array inside the library (about 1.1 MiB, reserved on
+ * every GPU that loads the library until the process exits). Nothing is allocated, on the
+ * device or the host. median/mad (nullable) receive the per-window M and D directly.
+ *
+ * Limits: at most RFI_NOALLOC_MAX_STREAMS streams and RFI_NOALLOC_MAX_TILES work-list entries
+ * (a tile holds as many whole windows as fit in a stage of up to 227 KiB); beyond them the call
+ * returns RFI_ERR_UNSUPPORTED before enqueueing anything.
+ *
+ * The first call on a device looks up the device address of the fixed array (once per device,
+ * with that device current); make it before any stream capture. All calls share the array and
+ * it keeps the last call's contents (the counters are cleared at the start of each call), so
+ * calls that overlap on the GPU race: serialise them. Asynchronous on `stream` unless totals is
+ * non-NULL, in which case the call synchronises `stream`, fills *totals and returns the device
+ * status (RFI_OK, RFI_ERR_SAMPLE_RANGE, RFI_ERR_TIMEOUT). */
+#define RFI_NOALLOC_MAX_STREAMS 64
+#define RFI_NOALLOC_MAX_TILES 65536
+RFI_API rfi_status rfi_excise_noalloc(const rfi_plan_desc *desc, const void *const *in, void *const *out,
+                                      uint32_t *const *mask, uint32_t *const *counts,
+                                      int32_t *const *median, int32_t *const *mad, rfi_totals *totals,
+                                      void *stream);
+
 /* Static description of a status code. */
 RFI_API const char *rfi_status_string(rfi_status status);
 

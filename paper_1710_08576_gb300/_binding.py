@@ -78,6 +78,8 @@ def _load():
         "rfi_excise_host": (ctypes.c_int, [_P, _PP, _PP, _PP, _PP, _P]),
         "rfi_stats": (ctypes.c_int, [_P, _PP, _PP, ctypes.POINTER(RfiTotals), _P]),
         "rfi_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(RfiPlanInfo)]),
+        "rfi_excise_noalloc": (ctypes.c_int, [ctypes.POINTER(RfiPlanDesc), _PP, _PP, _PP, _PP, _PP, _PP,
+                                              ctypes.POINTER(RfiTotals), _P]),
         "rfi_plan_destroy": (ctypes.c_int, [_P]),
         "rfi_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "rfi_version": (ctypes.c_char_p, []),
@@ -172,6 +174,16 @@ def rfi_stats(plan, medians=None, mads=None, stream=None):
     t = RfiTotals()
     a, b = _ptr_array(medians), _ptr_array(mads)
     st = LIB.rfi_stats(plan, a[0] if a else None, b[0] if b else None, ctypes.byref(t), _stream(stream))
+    return st, t
+
+
+def rfi_excise_noalloc(desc, ins, outs, masks=None, counts=None, medians=None, mads=None, totals=True,
+                       stream=None):
+    """Allocation-free excision (see include/rfi.h). Returns (status, totals or None)."""
+    arrs = [_ptr_array(x) for x in (ins, outs, masks, counts, medians, mads)]
+    t = RfiTotals() if totals else None
+    st = LIB.rfi_excise_noalloc(ctypes.byref(desc), *[a[0] if a else None for a in arrs],
+                                ctypes.byref(t) if t is not None else None, _stream(stream))
     return st, t
 
 
