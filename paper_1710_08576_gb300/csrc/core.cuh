@@ -26,9 +26,9 @@
 // difference, a three-operation byte compare against t, a byte permute that replicates each
 // byte's flag bit into 0x00/0xFF, and a byte dot product that packs the flags into mask bits.
 //
-// Digital-noise replacement is compacted per warp: each round of 32 chunks writes its
-// flagged positions to a per-warp shared list, and the warp then evaluates Philox for 32
-// listed samples at a time, so no lane idles while another one runs a long noise loop.
+// Digital-noise replacement is compacted per warp: each lane keeps the flag masks of four
+// rounds of chunks, then the warp numbers the flagged samples and all 32 lanes evaluate Philox
+// for 32 of them at a time, so no lane idles while another one runs a long noise loop.
 
 #pragma once
 
@@ -195,8 +195,6 @@ struct Geo {
 // there and its atomics use it as an immediate offset; kernels check it at entry.
 constexpr uint32_t kDynSmemShared = 1024;
 
-constexpr int kNoiseListPerWarp = 512;  // positions per warp per round (32 chunks x 16 samples)
-
 __device__ __forceinline__ int pad32(int b) { return b + (b >> 5); }
 
 struct __align__(16) RepShared {
@@ -231,7 +229,6 @@ struct Shm {
     uint32_t grp;        // 8-bit: byte offset of this group's half row (0 or 128)
     uint32_t *cum;       // padded cumulative counts
     Ctl *ctl;
-    uint16_t *nlist;     // noise positions, kNoiseListPerWarp per consumer warp
     int ncopies;         // 12-bit only
     int bar_id;          // named barrier of this consumer group
 };
@@ -559,14 +556,33 @@ __device__ __forceinline__ uint32_t chunk_bits(uint32_t f0, uint32_t f1, uint32_
     return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 8);
 }
 
-// Noise values for the flagged positions `bits` of chunk c of each lane: compacted through the
-// warp's shared list so that all 32 lanes evaluate Philox together. Stores go straight to the
-// output; they follow the chunk's own store in warp order (__syncwarp).
-template <int BITS>
-__device__ __forceinline__ void noise_round(const Win &w, const Rep &r, const Params &p, uint16_t *list,
-                                            int lane, int c, uint32_t bits) {
+// Position of the j-th (0-based) set bit of m (j < popc(m)), by halving popcount search.
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int j) {
+    int pos = 0;
+    int c = __popc(m & 0xFFFFu);
+    if (j >= c) { j -= c; pos += 16; m >>= 16; }
+    c = __popc(m & 0xFFu);
+    if (j >= c) { j -= c; pos += 8; m >>= 8; }
+    c = __popc(m & 0xFu);
+    if (j >= c) { j -= c; pos += 4; m >>= 4; }
+    c = __popc(m & 0x3u);
+    if (j >= c) { j -= c; pos += 2; m >>= 2; }
+    return pos + ((j >= static_cast<int>(m & 1u)) ? 1 : 0);
+}
+
+// Digital noise for the flagged samples of up to four rounds of the warp. Lane l holds in nb
+// the 16-bit flag masks of its chunks c0 + k*T (k = 0..3, mask k in bits [16k, 16k+16)). The
+// flagged samples are numbered across the warp (an exclusive prefix sum of the per-lane
+// counts); in each pass lane q takes sample q, found by a shuffle binary search for the lane
+// that owns it and a popcount search for its bit, and all 32 lanes evaluate Philox together.
+// The stores go straight to the output; they follow the chunks' own stores in warp order
+// (__syncwarp before the call).
+template <int BITS, int T>
+__device__ __forceinline__ void noise_batch(const Win &w, const Rep &r, const Params &p, int lane, int c0,
+                                            uint64_t nb) {
     constexpr int CS = Geo<BITS>::kChunkSamples;
-    const uint32_t cnt = __popc(bits);
+    const uint32_t lo = static_cast<uint32_t>(nb), hi = static_cast<uint32_t>(nb >> 32);
+    const uint32_t cnt = __popc(lo) + __popc(hi);
     uint32_t inc = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -574,22 +590,47 @@ __device__ __forceinline__ void noise_round(const Win &w, const Rep &r, const Pa
         if (lane >= o) inc += y;
     }
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
-    if (total == 0) return;
-    uint32_t off = inc - cnt;
-    uint32_t m = bits;
-    while (m) {
-        const int j = __ffs(m) - 1;
-        m &= m - 1u;
-        list[off++] = static_cast<uint16_t>(c * CS + j);
+    const uint32_t excl = inc - cnt;
+    for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        // owner: the last lane whose first index is <= q (lanes without flags share the next
+        // lane's first index, so the search passes over them)
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t e = __shfl_sync(0xFFFFFFFFu, excl, L + step);
+            if (e <= q) L += step;
+        }
+        const uint32_t eL = __shfl_sync(0xFFFFFFFFu, excl, L);
+        const uint32_t loL = __shfl_sync(0xFFFFFFFFu, lo, L);
+        const uint32_t hiL = __shfl_sync(0xFFFFFFFFu, hi, L);
+        const int cL = __shfl_sync(0xFFFFFFFFu, c0, L);
+        if (q < total) {
+            const int j = static_cast<int>(q - eL);
+            const int clo = __popc(loL);
+            const bool inlo = j < clo;
+            const int bp = (inlo ? 0 : 32) + nth_set_bit(inlo ? loL : hiL, inlo ? j : j - clo);
+            const int pos = (cL + (bp >> 4) * T) * CS + (bp & 15);
+            const int32_t z = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pos, Geo<BITS>::kLo, Geo<BITS>::kHi);
+            if (BITS == 8) w.out[pos] = static_cast<uint8_t>(z);
+            else reinterpret_cast<int16_t *>(w.out)[pos] = static_cast<int16_t>(z);
+        }
     }
-    __syncwarp();
-    for (uint32_t i = lane; i < total; i += 32) {
-        const int pos = list[i];
-        const int32_t z = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pos, Geo<BITS>::kLo, Geo<BITS>::kHi);
-        if (BITS == 8) w.out[pos] = static_cast<uint8_t>(z);
-        else reinterpret_cast<int16_t *>(w.out)[pos] = static_cast<int16_t>(z);
+}
+
+// Collects a round's flag masks for noise_batch; every fourth round (and at the end) it runs
+// the batch. nb/nk/c0 are the lane's batch state (nk warp-uniform).
+template <int BITS, int T>
+__device__ __forceinline__ void noise_collect(const Win &w, const Rep &r, const Params &p, int lane, int c,
+                                              uint32_t bits, uint64_t &nb, int &nk, int &c0) {
+    if (nk == 0) c0 = c;
+    nb |= static_cast<uint64_t>(bits) << (16 * nk);
+    if (++nk == 4) {
+        __syncwarp();
+        if (__any_sync(0xFFFFFFFFu, nb != 0)) noise_batch<BITS, T>(w, r, p, lane, c0, nb);
+        nb = 0;
+        nk = 0;
     }
-    __syncwarp();
 }
 
 template <int BITS, int MODE, int T>
@@ -601,7 +642,8 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
     const int nfull = nbytes >> 4;
     const int nchunks = (nbytes + 15) >> 4;
     const uint4 *d4 = reinterpret_cast<const uint4 *>(w.data);
-    uint16_t *list = sm.nlist + warp * kNoiseListPerWarp;
+    uint64_t nb = 0;  // digital noise: flag masks of up to four rounds
+    int nk = 0, c0 = 0;
     uint32_t flagged = 0;
     if (BITS == 8) {
         const uint4 *rq = reinterpret_cast<const uint4 *>(&sm.ctl->rep);
@@ -633,10 +675,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 __stcs(o4 + c, v);
                 mk[c] = static_cast<uint16_t>(bits);
                 flagged += __popc(bits);
-                if (MODE == 3) {
-                    __syncwarp();
-                    noise_round<8>(w, r, p, list, lane, c, bits);
-                }
+                if (MODE == 3) noise_collect<8, T>(w, r, p, lane, c, bits, nb, nk, c0);
             }
         }
         // warp-uniform rounds: lane handles chunk base + lane
@@ -671,13 +710,14 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 flagged += __popc(bits);
                 if (mk) mk[c] = static_cast<uint16_t>(bits);
             }
-            if (MODE == 3) {
-                __syncwarp();
-                noise_round<8>(w, r, p, list, lane, c, bits);
-            }
+            if (MODE == 3) noise_collect<8, T>(w, r, p, lane, c, bits, nb, nk, c0);
         }
         if (mk) {
             for (int c = nchunks + tid; c < 2 * w.mask_words; c += T) mk[c] = 0;
+        }
+        if (MODE == 3 && nk) {
+            __syncwarp();
+            if (__any_sync(0xFFFFFFFFu, nb != 0)) noise_batch<8, T>(w, r, p, lane, c0, nb);
         }
     } else {
         uint8_t *mk = reinterpret_cast<uint8_t *>(w.mask);
@@ -714,13 +754,14 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 }
                 if (mk) mk[c] = static_cast<uint8_t>(bits);
             }
-            if (MODE == 3) {
-                __syncwarp();
-                noise_round<12>(w, r, p, list, lane, c, bits);
-            }
+            if (MODE == 3) noise_collect<12, T>(w, r, p, lane, c, bits, nb, nk, c0);
         }
         if (mk) {
             for (int c = nchunks + tid; c < 4 * w.mask_words; c += T) mk[c] = 0;
+        }
+        if (MODE == 3 && nk) {
+            __syncwarp();
+            if (__any_sync(0xFFFFFFFFu, nb != 0)) noise_batch<12, T>(w, r, p, lane, c0, nb);
         }
     }
     return flagged;

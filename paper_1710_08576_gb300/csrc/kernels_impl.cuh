@@ -25,24 +25,22 @@ struct StageMeta {
 
 // Dynamic shared memory: the histogram at offset 0 (8-bit: one 64 KiB table for all groups;
 // 12-bit: per group), then one block per consumer group (cumulative counts, control block,
-// noise lists, mbarriers, stage descriptors), then the stage buffers of every group.
+// mbarriers, stage descriptors), then the stage buffers of every group.
 struct Layout {
     int grp;        // first group block
     int grp_size;   // bytes per group block
-    int cum, ctl, nlist, bar, meta;  // offsets inside a group block
+    int cum, ctl, bar, meta;  // offsets inside a group block
     int stage;      // first stage buffer; group g stage s at stage + (g * stages + s) * stage_bytes
     int total;
 };
 
-// The noise lists exist only for digital-noise replacement (mode 3).
 template <int BITS>
 __host__ __device__ inline Layout layout(int ncopies, int stages, int stage_bytes, int cw, int groups, int mode) {
     Layout L;
     L.grp = align_up(Geo<BITS>::hist_bytes(ncopies, groups), 128);
     L.cum = 0;
     L.ctl = align_up(Geo<BITS>::kCumWords * 4, 128);
-    L.nlist = align_up(L.ctl + static_cast<int>(sizeof(Ctl)), 128);
-    L.bar = align_up(L.nlist + (mode == 3 ? cw * kNoiseListPerWarp * 2 : 0), 128);
+    L.bar = align_up(L.ctl + static_cast<int>(sizeof(Ctl)), 128);
     L.meta = align_up(L.bar + (2 * kMaxStages + 1) * 8, 128);
     L.grp_size = align_up(L.meta + kMaxStages * static_cast<int>(sizeof(StageMeta)), 128);
     L.stage = L.grp + groups * L.grp_size;
@@ -60,7 +58,6 @@ __device__ __forceinline__ Shm group_view(uint8_t *smem, const Layout &L, int g,
     sm.grp = BITS == 8 ? 128u * static_cast<uint32_t>(g) : 0u;
     sm.cum = reinterpret_cast<uint32_t *>(gb + L.cum);
     sm.ctl = reinterpret_cast<Ctl *>(gb + L.ctl);
-    sm.nlist = reinterpret_cast<uint16_t *>(gb + L.nlist);
     sm.ncopies = ncopies;
     sm.bar_id = 1 + g;
     return sm;
