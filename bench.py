@@ -195,38 +195,20 @@ def run_ours(args):
     import synth
     from synth import workloads
 
-    rank, local, world = env_rank()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1710_08576_gb300 import dist as rdist
+
+    rank, local, world = rdist.env_rank()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    group = rdist.Group("nccl" if world > 1 else None, device=dev)
+    barrier, max_over_ranks, sum_over_ranks = group.barrier, group.max, group.sum
 
     W = 16384
     w = workloads.gwb60(length=args.length, nstreams=args.streams)
     # each rank excises its own 60-stream batch (a different antenna set): weak scaling
+    sids = rdist.stream_ids(rank, len(w.streams))
     t_gen = time.perf_counter()
-    xs = [synth.fill(s.feed, s.index + 1000 * rank, s.length) for s in w.streams]
+    xs = [synth.fill(s.feed, sid, s.length) for s, sid in zip(w.streams, sids)]
     t_gen = time.perf_counter() - t_gen
     S = len(xs)
     lens = [x.size for x in xs]
@@ -240,10 +222,10 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
 
     batched = [rfi.Plan(8, lens, [W] * S, v.k, v.mode, v.const, v.seed,
-                        rfi.RFI_PLAN_GRAPH | rfi.RFI_PLAN_AUTOTUNE, [s.index + 1000 * rank for s in w.streams])
+                        rfi.RFI_PLAN_GRAPH | rfi.RFI_PLAN_AUTOTUNE, sids)
                for v in w.variants]
-    per_stream = [rfi.Plan(8, lens, [W] * S, v.k, v.mode, v.const, v.seed, rfi.RFI_PLAN_PER_STREAM,
-                           [s.index + 1000 * rank for s in w.streams]) for v in w.variants]
+    per_stream = [rfi.Plan(8, lens, [W] * S, v.k, v.mode, v.const, v.seed, rfi.RFI_PLAN_PER_STREAM, sids)
+                  for v in w.variants]
     info = batched[0].info()
 
     def timed(plans, steps, warmup, per_call_events=True):
@@ -365,8 +347,7 @@ def run_ours(args):
             "clocks": clocks_b,
         }
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    group.close()
     return 0
 
 
