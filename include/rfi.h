@@ -197,6 +197,124 @@ RFI_API rfi_status rfi_excise_noalloc(const rfi_plan_desc *desc, const void *con
                                       int32_t *const *median, int32_t *const *mad, rfi_totals *totals,
                                       void *stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Serving: real-time excision of sample streams fed in chunks, plus backfill requests, with
+ * continuous batching on one GPU (the GWB feeds 60 inputs at 800 Msps each, Section II-C).
+ *
+ * A server owns one device arena of memory_budget bytes. Each stream s has device rings of
+ * ring_samples samples (rounded up to a multiple of W_s) for its input, output, mask, counts,
+ * median and MAD. rfi_server_push appends a chunk (host or device memory) at the stream's
+ * produced position, or returns RFI_ERR_BUSY when the ring has no room (samples whose output was
+ * not yet read and released). rfi_server_submit admits a backfill request (an independent
+ * buffer excised like a stream slice starting at absolute index abs0) into a free request slot;
+ * a host request also needs room in the arena for its device copies; otherwise RFI_ERR_BUSY (or
+ * RFI_ERR_OOM if it can never fit). rfi_server_step launches one persistent-kernel pass over
+ * every complete window that has arrived on every ring plus a bounded slice of every admitted
+ * request, as long as fewer than two passes are in flight; work that arrives while a pass runs
+ * joins the next one. rfi_server_poll reports whether a chunk or request is done and its latency
+ * (push/submit to completion of its last window, on the device clock; a host request's also
+ * covers the copy of its results back). rfi_server_read copies
+ * excised output of a stream out of the ring and may release it. Output equals the plan path on
+ * the whole stream: windows are aligned to absolute multiples of W_s and the digital noise is
+ * keyed by the absolute sample index, so chunking, batching and the mix of concurrent work do
+ * not change any result.
+ *
+ * Checkpoint and resume: rfi_server_position returns, per stream, the absolute index up to which
+ * output is complete (a window boundary). A new server created with stream_start = that index,
+ * fed from that index on, continues bit for bit.
+ *
+ * Memory and ordering: the server's copies run on its own non-blocking streams, so device
+ * samples passed to push or submit must be complete (their producer synchronised) before the
+ * call, and a pushed device buffer may be reused once its chunk's ticket is done. Host chunks and host requests
+ * are copied from the caller's memory (pinned memory keeps those copies asynchronous; pageable
+ * memory makes them synchronous). A device request's in/out/mask/counts must stay valid until
+ * its ticket is done. Reads return after their copy completed.
+ *
+ * A server is used from one host thread; all calls are synchronous with respect to the host
+ * except the device work itself. Errors: RFI_ERR_INVALID_ARG for out-of-range arguments (checked
+ * before any CUDA call), RFI_ERR_BUSY for back-pressure (retry after step/read), RFI_ERR_OOM
+ * when the budget cannot hold the rings (create) or a host request (submit), RFI_ERR_CUDA when
+ * a CUDA call fails; device-side errors (a 12-bit sample out of range, a timed-out wait) latch
+ * into rfi_server_stats.device_status. */
+typedef struct rfi_server_s *rfi_server_t;
+
+typedef struct rfi_server_desc {
+    int32_t sample_bits;             /* 8 or 12 */
+    int32_t num_streams;             /* S >= 1 */
+    const int32_t *window_len;       /* [S] W_s in [1, 65536] */
+    const uint32_t *stream_id;       /* [S] Philox stream key; NULL means 0..S-1 */
+    const int64_t *stream_start;     /* [S] absolute index of the first sample, a multiple of
+                                        W_s (resume point); NULL means 0 */
+    int64_t ring_samples;            /* per-stream ring capacity, >= W_s */
+    double k;                        /* threshold multiple, as rfi_plan_desc */
+    int32_t mode;                    /* rfi_mode */
+    int32_t const_value;
+    uint64_t seed;
+    uint64_t memory_budget;          /* device bytes for rings, per-pass buffers and requests */
+    int32_t max_requests;            /* request slots, >= 1 */
+    int32_t request_windows_per_step;/* windows of one request per pass; 0 means 1024 */
+} rfi_server_desc;
+
+typedef struct rfi_request_desc {
+    const void *in;                  /* samples, host or device (on_device) */
+    void *out;                       /* output, same memory kind; may equal in */
+    uint32_t *mask;                  /* nullable; layout as rfi_excise */
+    uint32_t *counts;                /* nullable */
+    int64_t len;                     /* samples, >= 1 */
+    int32_t window_len;              /* W in [1, 65536] */
+    uint32_t stream_id;              /* Philox stream key */
+    int64_t abs0;                    /* absolute index of in[0], a multiple of W */
+    int32_t on_device;               /* 1: device pointers; 0: host pointers (copied by the server) */
+} rfi_request_desc;
+
+typedef struct rfi_server_stats {
+    uint64_t passes;                 /* kernel passes launched */
+    uint64_t chunks_done, requests_done;
+    uint64_t samples_done;           /* ring samples excised */
+    uint64_t request_samples_done;
+    uint64_t flagged;
+    double chunk_latency_p50_us, chunk_latency_p99_us, chunk_latency_max_us;
+    double request_latency_p50_us, request_latency_p99_us;
+    double wall_seconds;             /* first push or submit to the last completion */
+    uint64_t arena_bytes, arena_peak_bytes;
+    int32_t device_status;           /* rfi_status latched by any pass */
+    double gpu_busy_seconds;         /* sum of pass durations on the device clock */
+} rfi_server_stats;
+
+RFI_API rfi_status rfi_server_create(const rfi_server_desc *desc, rfi_server_t *server);
+RFI_API rfi_status rfi_server_push(rfi_server_t server, int32_t stream, const void *samples, int64_t n,
+                                   int32_t on_device, uint64_t *ticket);
+RFI_API rfi_status rfi_server_submit(rfi_server_t server, const rfi_request_desc *req, uint64_t *ticket);
+RFI_API rfi_status rfi_server_step(rfi_server_t server, int32_t *launched);
+RFI_API rfi_status rfi_server_poll(rfi_server_t server, uint64_t ticket, int32_t *done, double *latency_us);
+/* Copy output samples [start, start+n) of a stream (start, n whole windows except at a flushed
+ * end; start >= the released position; start+n <= the completed position) to dst and, if
+ * mask_dst != NULL, their mask words; release != 0 frees that ring space (start must then equal
+ * the released position). */
+RFI_API rfi_status rfi_server_read(rfi_server_t server, int32_t stream, int64_t start, int64_t n, void *dst,
+                                   uint32_t *mask_dst, int32_t on_device, int32_t release);
+/* Zero-copy consumer: device pointers to the ring's output (and mask words) from `start` (a
+ * window boundary in [released, completed]) and the number n of samples readable there before
+ * the completed position or the ring's wrap. They stay valid until the range is released. */
+RFI_API rfi_status rfi_server_view(rfi_server_t server, int32_t stream, int64_t start, const void **out,
+                                   const uint32_t **mask, int64_t *n);
+/* Release a stream's output up to `upto` (a window boundary, or the completed end of a flushed
+ * stream, in [released, completed]) without copying it. */
+RFI_API rfi_status rfi_server_release(rfi_server_t server, int32_t stream, int64_t upto);
+/* Move up to cap latency records (ticket, microseconds) of finished chunks and requests out of
+ * the server, oldest first; *n gets the number moved. A taken ticket no longer polls as done;
+ * the stats percentiles keep every record. */
+RFI_API rfi_status rfi_server_take_latencies(rfi_server_t server, uint64_t *tickets, double *latency_us,
+                                             int64_t cap, int64_t *n);
+/* End of stream: the next pass also excises the last, partial window; no more pushes after. */
+RFI_API rfi_status rfi_server_flush(rfi_server_t server, int32_t stream);
+RFI_API rfi_status rfi_server_position(rfi_server_t server, int32_t stream, int64_t *produced, int64_t *completed,
+                                       int64_t *released);
+/* Step and poll until all admitted work is done (bounded by timeout_seconds). */
+RFI_API rfi_status rfi_server_drain(rfi_server_t server, double timeout_seconds);
+RFI_API rfi_status rfi_server_get_stats(rfi_server_t server, rfi_server_stats *stats);
+RFI_API rfi_status rfi_server_destroy(rfi_server_t server);
+
 /* Static description of a status code. */
 RFI_API const char *rfi_status_string(rfi_status status);
 

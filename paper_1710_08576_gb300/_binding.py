@@ -59,8 +59,36 @@ class RfiPlanInfo(ctypes.Structure):
                 ("sm_count", ctypes.c_int32), ("kernels_per_call", ctypes.c_int32)]
 
 
+class RfiServerDesc(ctypes.Structure):
+    _fields_ = [("sample_bits", ctypes.c_int32), ("num_streams", ctypes.c_int32),
+                ("window_len", ctypes.POINTER(ctypes.c_int32)),
+                ("stream_id", ctypes.POINTER(ctypes.c_uint32)),
+                ("stream_start", ctypes.POINTER(ctypes.c_int64)), ("ring_samples", ctypes.c_int64),
+                ("k", ctypes.c_double), ("mode", ctypes.c_int32), ("const_value", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("memory_budget", ctypes.c_uint64),
+                ("max_requests", ctypes.c_int32), ("request_windows_per_step", ctypes.c_int32)]
+
+
+class RfiRequestDesc(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("counts", ctypes.c_void_p), ("len", ctypes.c_int64), ("window_len", ctypes.c_int32),
+                ("stream_id", ctypes.c_uint32), ("abs0", ctypes.c_int64), ("on_device", ctypes.c_int32)]
+
+
+class RfiServerStats(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_uint64), ("chunks_done", ctypes.c_uint64),
+                ("requests_done", ctypes.c_uint64), ("samples_done", ctypes.c_uint64),
+                ("request_samples_done", ctypes.c_uint64), ("flagged", ctypes.c_uint64),
+                ("chunk_latency_p50_us", ctypes.c_double), ("chunk_latency_p99_us", ctypes.c_double),
+                ("chunk_latency_max_us", ctypes.c_double), ("request_latency_p50_us", ctypes.c_double),
+                ("request_latency_p99_us", ctypes.c_double), ("wall_seconds", ctypes.c_double),
+                ("arena_bytes", ctypes.c_uint64), ("arena_peak_bytes", ctypes.c_uint64),
+                ("device_status", ctypes.c_int32), ("gpu_busy_seconds", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _PP = ctypes.POINTER(ctypes.c_void_p)
+_I64P = ctypes.POINTER(ctypes.c_int64)
 
 
 def _load():
@@ -81,6 +109,25 @@ def _load():
         "rfi_excise_noalloc": (ctypes.c_int, [ctypes.POINTER(RfiPlanDesc), _PP, _PP, _PP, _PP, _PP, _PP,
                                               ctypes.POINTER(RfiTotals), _P]),
         "rfi_plan_destroy": (ctypes.c_int, [_P]),
+        "rfi_server_create": (ctypes.c_int, [ctypes.POINTER(RfiServerDesc), ctypes.POINTER(_P)]),
+        "rfi_server_push": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+        "rfi_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(RfiRequestDesc), ctypes.POINTER(ctypes.c_uint64)]),
+        "rfi_server_step": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+        "rfi_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_double)]),
+        "rfi_server_read": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _P,
+                                           ctypes.c_int32, ctypes.c_int32]),
+        "rfi_server_view": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, _PP,
+                                           ctypes.POINTER(ctypes.POINTER(ctypes.c_uint32)), _I64P]),
+        "rfi_server_release": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
+        "rfi_server_take_latencies": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64),
+                                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int64, _I64P]),
+        "rfi_server_flush": (ctypes.c_int, [_P, ctypes.c_int32]),
+        "rfi_server_position": (ctypes.c_int, [_P, ctypes.c_int32, _I64P, _I64P, _I64P]),
+        "rfi_server_drain": (ctypes.c_int, [_P, ctypes.c_double]),
+        "rfi_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(RfiServerStats)]),
+        "rfi_server_destroy": (ctypes.c_int, [_P]),
         "rfi_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "rfi_version": (ctypes.c_char_p, []),
     }
@@ -205,6 +252,85 @@ def rfi_version() -> str:
     return LIB.rfi_version().decode()
 
 
+def rfi_server_create(desc: RfiServerDesc):
+    h = ctypes.c_void_p()
+    st = LIB.rfi_server_create(ctypes.byref(desc), ctypes.byref(h))
+    return st, h.value
+
+
+def rfi_server_push(server, stream, samples, n, on_device=True):
+    t = ctypes.c_uint64()
+    st = LIB.rfi_server_push(server, int(stream), _ptr(samples), int(n), int(bool(on_device)), ctypes.byref(t))
+    return st, t.value
+
+
+def rfi_server_submit(server, req: RfiRequestDesc):
+    t = ctypes.c_uint64()
+    st = LIB.rfi_server_submit(server, ctypes.byref(req), ctypes.byref(t))
+    return st, t.value
+
+
+def rfi_server_step(server):
+    launched = ctypes.c_int32()
+    st = LIB.rfi_server_step(server, ctypes.byref(launched))
+    return st, launched.value
+
+
+def rfi_server_poll(server, ticket):
+    done, lat = ctypes.c_int32(), ctypes.c_double()
+    st = LIB.rfi_server_poll(server, int(ticket), ctypes.byref(done), ctypes.byref(lat))
+    return st, bool(done.value), lat.value
+
+
+def rfi_server_read(server, stream, start, n, dst, mask_dst=None, on_device=True, release=True):
+    return LIB.rfi_server_read(server, int(stream), int(start), int(n), _ptr(dst), _ptr(mask_dst) or None,
+                               int(bool(on_device)), int(bool(release)))
+
+
+def rfi_server_view(server, stream, start):
+    out, mask, n = ctypes.c_void_p(), ctypes.POINTER(ctypes.c_uint32)(), ctypes.c_int64()
+    st = LIB.rfi_server_view(server, int(stream), int(start), ctypes.byref(out), ctypes.byref(mask),
+                             ctypes.byref(n))
+    mptr = ctypes.cast(mask, ctypes.c_void_p).value if mask else 0
+    return st, out.value or 0, mptr or 0, n.value
+
+
+def rfi_server_release(server, stream, upto):
+    return LIB.rfi_server_release(server, int(stream), int(upto))
+
+
+def rfi_server_take_latencies(server, cap=65536):
+    t = (ctypes.c_uint64 * cap)()
+    lat = (ctypes.c_double * cap)()
+    n = ctypes.c_int64()
+    st = LIB.rfi_server_take_latencies(server, t, lat, int(cap), ctypes.byref(n))
+    return st, list(t[:n.value]), list(lat[:n.value])
+
+
+def rfi_server_flush(server, stream):
+    return LIB.rfi_server_flush(server, int(stream))
+
+
+def rfi_server_position(server, stream):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    st = LIB.rfi_server_position(server, int(stream), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return st, a.value, b.value, c.value
+
+
+def rfi_server_drain(server, timeout_seconds=60.0):
+    return LIB.rfi_server_drain(server, float(timeout_seconds))
+
+
+def rfi_server_get_stats(server):
+    s = RfiServerStats()
+    st = LIB.rfi_server_get_stats(server, ctypes.byref(s))
+    return st, s
+
+
+def rfi_server_destroy(server):
+    return LIB.rfi_server_destroy(server)
+
+
 # ---------------------------------------------------------------- convenience wrapper
 class RfiError(RuntimeError):
     def __init__(self, status: int, what: str):
@@ -269,3 +395,95 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Server:
+    """Owns one rfi_server_t (real-time rings + backfill requests, continuous batching)."""
+
+    def __init__(self, bits, window_len, ring_samples, k, mode, const_value=0, seed=0,
+                 memory_budget=1 << 30, max_requests=4, request_windows_per_step=0,
+                 stream_id=None, stream_start=None):
+        n = len(window_len)
+        self._keep = [(ctypes.c_int32 * n)(*[int(v) for v in window_len])]
+        sid = start = None
+        if stream_id is not None:
+            sid = (ctypes.c_uint32 * n)(*[int(v) for v in stream_id])
+            self._keep.append(sid)
+        if stream_start is not None:
+            start = (ctypes.c_int64 * n)(*[int(v) for v in stream_start])
+            self._keep.append(start)
+        self.desc = RfiServerDesc(int(bits), n, self._keep[0], sid, start, int(ring_samples), float(k),
+                                  int(mode), int(const_value), int(seed), int(memory_budget),
+                                  int(max_requests), int(request_windows_per_step))
+        st, h = rfi_server_create(self.desc)
+        check(st, "rfi_server_create")
+        self.handle = h
+        self.bits = bits
+
+    def push(self, stream, samples, n=None, on_device=True):
+        n = samples.numel() if n is None else n
+        return rfi_server_push(self.handle, stream, samples, n, on_device)
+
+    def submit(self, inp, out, window_len, stream_id=0, abs0=0, mask=None, counts=None, on_device=True):
+        n = inp.numel() if hasattr(inp, "numel") else inp.size
+        req = RfiRequestDesc(_ptr(inp), _ptr(out), _ptr(mask) or None, _ptr(counts) or None, int(n),
+                             int(window_len), int(stream_id), int(abs0), int(bool(on_device)))
+        return rfi_server_submit(self.handle, req)
+
+    def step(self):
+        st, launched = rfi_server_step(self.handle)
+        check(st, "rfi_server_step")
+        return launched
+
+    def poll(self, ticket):
+        st, done, lat = rfi_server_poll(self.handle, ticket)
+        check(st, "rfi_server_poll")
+        return done, lat
+
+    def read(self, stream, start, n, dst, mask_dst=None, on_device=True, release=True):
+        return rfi_server_read(self.handle, stream, start, n, dst, mask_dst, on_device, release)
+
+    def flush(self, stream):
+        check(rfi_server_flush(self.handle, stream), "rfi_server_flush")
+
+    def view(self, stream, start):
+        """(status, output device pointer, mask device pointer, samples readable there)."""
+        return rfi_server_view(self.handle, stream, start)
+
+    def release(self, stream, upto):
+        return rfi_server_release(self.handle, stream, upto)
+
+    def take_latencies(self, cap=65536):
+        """All finished (ticket, latency us) records not yet taken, oldest first."""
+        tickets, lats = [], []
+        while True:
+            st, t, l = rfi_server_take_latencies(self.handle, cap)
+            check(st, "rfi_server_take_latencies")
+            tickets += t
+            lats += l
+            if len(t) < cap:
+                return tickets, lats
+
+    def position(self, stream):
+        st, p, c, r = rfi_server_position(self.handle, stream)
+        check(st, "rfi_server_position")
+        return p, c, r
+
+    def drain(self, timeout_seconds=120.0):
+        check(rfi_server_drain(self.handle, timeout_seconds), "rfi_server_drain")
+
+    def stats(self):
+        st, s = rfi_server_get_stats(self.handle)
+        check(st, "rfi_server_get_stats")
+        return s
+
+    def close(self):
+        if self.handle:
+            rfi_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -11,6 +11,13 @@ constexpr uint32_t kStatusSampleRange = 1u;  // reported as RFI_ERR_SAMPLE_RANGE
 constexpr uint32_t kStatusTimeout = 2u;      // reported as RFI_ERR_TIMEOUT
 constexpr uint32_t kStatusLayout = 4u;       // unexpected shared-memory window: RFI_ERR_UNSUPPORTED
 
+// Device counters of one kernel pass, reset before it.
+struct DevCounters {
+    unsigned tile_counter;       // dynamic work-list cursor
+    uint32_t status;             // kStatus* bits
+    unsigned long long flagged;  // flagged samples of the pass
+};
+
 // One contiguous run of windows of one stream, starting on a window boundary.
 struct Seg {
     const uint8_t *in;    // sample 0 of the run

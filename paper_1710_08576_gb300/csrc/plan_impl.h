@@ -11,13 +11,6 @@
 
 namespace rfi {
 
-// Device counters reset before every call.
-struct DevCounters {
-    unsigned tile_counter;       // dynamic work-list cursor
-    uint32_t status;             // kStatus* bits
-    unsigned long long flagged;  // flagged samples of the call
-};
-
 // Buffers of the chunked host pipeline (rfi_excise_host), allocated on first use.
 struct HostPipe {
     static constexpr int kSlots = 3;

@@ -92,3 +92,38 @@ def test_status_strings():
         assert rfi.rfi_status_string(s) and rfi.rfi_status_string(s) != "unknown status"
     assert rfi.rfi_status_string(99) == "unknown status"
     assert "sm_103a" in rfi.rfi_version()
+
+
+def test_server_layouts_match_header(tmp_path):
+    src = tmp_path / "srv.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "rfi.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(rfi_server_desc), sizeof(rfi_request_desc), sizeof(rfi_server_stats),
+         offsetof(rfi_server_desc, memory_budget), offsetof(rfi_request_desc, abs0),
+         offsetof(rfi_server_stats, device_status));
+  return 0;
+}''')
+    exe = tmp_path / "srv"
+    subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)], text=True).split()]
+    C = ctypes
+    assert got == [C.sizeof(rfi.RfiServerDesc), C.sizeof(rfi.RfiRequestDesc), C.sizeof(rfi.RfiServerStats),
+                   rfi.RfiServerDesc.memory_budget.offset, rfi.RfiRequestDesc.abs0.offset,
+                   rfi.RfiServerStats.device_status.offset]
+
+
+def test_server_invalid_arguments_fail_before_cuda():
+    n = 2
+    w = (ctypes.c_int32 * n)(1024, 0)
+    d = rfi.RfiServerDesc(8, n, w, None, None, 4096, 3.0, 0, 0, 0, 1 << 30, 1, 0)
+    assert rfi.rfi_server_create(d)[0] == rfi.RFI_ERR_INVALID_ARG
+    w = (ctypes.c_int32 * n)(1024, 2048)
+    d = rfi.RfiServerDesc(8, n, w, None, None, 1024, 3.0, 0, 0, 0, 1 << 30, 1, 0)  # ring < W
+    assert rfi.rfi_server_create(d)[0] == rfi.RFI_ERR_INVALID_ARG
+    starts = (ctypes.c_int64 * n)(0, 1000)  # not a multiple of W
+    d = rfi.RfiServerDesc(8, n, w, None, starts, 1 << 16, 3.0, 0, 0, 0, 1 << 30, 1, 0)
+    assert rfi.rfi_server_create(d)[0] == rfi.RFI_ERR_INVALID_ARG
+    assert rfi.LIB.rfi_server_destroy(None) == rfi.RFI_OK
