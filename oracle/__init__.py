@@ -1,4 +1,5 @@
-"""CPU oracle for windowed median/MAD RFI excision (Section II-D, Eq. 1 and Eq. 2).
+"""CPU oracle for windowed median/MAD RFI excision (Section II-D, Eq. 1 and Eq. 2) and its
+Median-of-MAD variant (Eq. 3).
 
 TEST INFRASTRUCTURE: only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
 baseline leg may import this package. The definition it computes, and every reading it takes
@@ -46,6 +47,9 @@ def lib():
             L.oracle_noise_value.restype = ctypes.c_int32
             L.oracle_noise_value.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                              ctypes.c_uint32, ctypes.c_int64, ctypes.c_int32]
+            L.oracle_excise_mom.restype = ctypes.c_int
+            L.oracle_excise_mom.argtypes = [ctypes.POINTER(OracleArgs), ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_void_p]
             L.oracle_median_mad.restype = None
             L.oracle_median_mad.argtypes = [ctypes.c_void_p, ctypes.c_int64,
                                             ctypes.POINTER(ctypes.c_int32),
@@ -77,6 +81,36 @@ def median_mad(x) -> tuple[int, int]:
     M, D = ctypes.c_int32(), ctypes.c_int32()
     lib().oracle_median_mad(a.ctypes.data, a.size, ctypes.byref(M), ctypes.byref(D))
     return M.value, D.value
+
+
+def excise_mom(x: np.ndarray, W: int, k: float, mode: int, k_mom: int, const: int = 0, seed: int = 0,
+               stream_id: int = 0, abs0: int = 0, bits: int | None = None, threads: int = 1,
+               history=None, want=("z", "mask", "counts", "median", "mad", "mom")):
+    """Median-of-MAD excision (Eq. 3) of one stream or slice; ``history`` is the MADs of the
+    windows just before the slice (oldest first, at most k_mom - 1). Returns excise()'s dict
+    plus ``mom``, the dispersion each window used."""
+    x = np.ascontiguousarray(x)
+    if bits is None:
+        bits = 8 if x.dtype == np.int8 else 12
+    assert x.dtype == (np.int8 if bits == 8 else np.int16)
+    n = x.size
+    nw = -(-n // W) if (n > 0 and W > 0) else 0
+    res = {"z": np.empty_like(x)}
+    res["mask"] = np.zeros(mask_words(W, nw), np.uint32) if "mask" in want else None
+    for key, dt in (("counts", np.uint32), ("median", np.int32), ("mad", np.int32), ("mom", np.int32)):
+        res[key] = np.zeros(nw, dt) if key in want else None
+    hist = np.ascontiguousarray(history if history is not None else np.zeros(0), dtype=np.int32)
+
+    def p(a):
+        return None if a is None else a.ctypes.data
+
+    args = OracleArgs(x.ctypes.data, res["z"].ctypes.data, bits, n, W, abs0, float(k), mode, const,
+                      seed, stream_id, p(res["mask"]), p(res["counts"]), p(res["median"]),
+                      p(res["mad"]), max(1, int(threads)))
+    res["status"] = int(lib().oracle_excise_mom(ctypes.byref(args), int(k_mom),
+                                                p(hist) if hist.size else None, int(hist.size),
+                                                p(res["mom"])))
+    return res
 
 
 def mask_words(W: int, n_windows: int) -> int:

@@ -7,7 +7,9 @@
 // CUDA path; every value it uses it derives here, from the paper or from the readings listed
 // below.
 //
-// What it computes, per non-overlapping data window of n samples (Section II-D):
+// What it computes, per non-overlapping data window of n samples (Section II-D), and the
+// Median-of-MAD variant (Eq. 3, oracle_excise_mom) that replaces D by the median of the MADs of
+// the last k_mom windows:
 //   M = M(x)                      median of the window (std::sort, lower median s[(n-1)/2])
 //   D = M(|x_i - M|)              median absolute deviation, same lower-median rule
 //   tau_U = M + n_s*(1.4826*D)    Eq. 1 (n_s is the paper's threshold multiple "n")
@@ -30,6 +32,11 @@
 //   * every replacement is saturated to the sample range ([-128,127] or [-2048,2047]).
 //   * windows start at absolute sample 0 of the stream; the last window may be shorter.
 //   * 12-bit input outside [-2048,2047] is an error (status 6).
+//   * Eq. 3 (Median of MAD): the k successive windows are the k_mom windows ending at the
+//     current one (causal, sliding by one window); at the start of a stream, the windows that
+//     exist. Lower median of those MADs. The thresholds stay centred on the window's own
+//     median; the MoM takes D's place in Eq. 1, in the threshold replacement and in the noise
+//     spread, and a MoM of 0 flags nothing.
 //
 // Build: g++ -O2 -std=c++17 -fPIC -shared -pthread (see build.py in this directory).
 
@@ -138,21 +145,47 @@ void store(const Job &j, int64_t i, int32_t v) {
     else ((int16_t *)j.z)[i] = (int16_t)v;
 }
 
-// One data window: samples [s0, s0+n) of the call; window number w.
-int excise_window(const Job &j, int64_t w) {
+// Samples of window w (samples [s0, s0+n) of the call); false if a 12-bit sample is out of range.
+bool window_samples(const Job &j, int64_t w, std::vector<int32_t> &x) {
     const int32_t lo = j.bits == 8 ? -128 : -2048, hi = j.bits == 8 ? 127 : 2047;
     const int64_t s0 = w * (int64_t)j.W;
     const int64_t n = std::min<int64_t>(j.W, j.len - s0);
-    std::vector<int32_t> x(n);
+    x.resize(n);
     for (int64_t i = 0; i < n; ++i) {
         x[i] = load(j, s0 + i);
-        if (x[i] < lo || x[i] > hi) return ORACLE_SAMPLE_RANGE;
+        if (x[i] < lo || x[i] > hi) return false;
     }
-    // robust estimation: median and median absolute deviation (Section II-D)
-    const int32_t M = lower_median(x);
-    std::vector<int32_t> dev(n);
-    for (int64_t i = 0; i < n; ++i) dev[i] = x[i] > M ? x[i] - M : M - x[i];
-    const int32_t D = lower_median(dev);
+    return true;
+}
+
+// Robust estimation of one window (Section II-D): its median M and median absolute deviation D.
+void window_stats(const std::vector<int32_t> &x, int32_t *M, int32_t *D) {
+    const int32_t m = lower_median(x);
+    std::vector<int32_t> dev(x.size());
+    for (size_t i = 0; i < x.size(); ++i) dev[i] = x[i] > m ? x[i] - m : m - x[i];
+    *M = m;
+    *D = lower_median(dev);
+}
+
+// Threshold detection and filtering of window w (Eq. 1, Eq. 2) around centre M with dispersion D.
+void apply_window(const Job &j, int64_t w, const std::vector<int32_t> &x, int32_t M, int32_t D);
+
+// One data window: samples [s0, s0+n) of the call; window number w.
+int excise_window(const Job &j, int64_t w) {
+    std::vector<int32_t> x;
+    if (!window_samples(j, w, x)) return ORACLE_SAMPLE_RANGE;
+    int32_t M, D;
+    window_stats(x, &M, &D);
+    apply_window(j, w, x, M, D);
+    if (j.median) j.median[w] = M;
+    if (j.mad) j.mad[w] = D;
+    return ORACLE_OK;
+}
+
+void apply_window(const Job &j, int64_t w, const std::vector<int32_t> &x, int32_t M, int32_t D) {
+    const int32_t lo = j.bits == 8 ? -128 : -2048, hi = j.bits == 8 ? 127 : 2047;
+    const int64_t s0 = w * (int64_t)j.W;
+    const int64_t n = (int64_t)x.size();
     // Eq. 1 in Q16: tau_U = M + Kq*D/2^16, tau_L = M - Kq*D/2^16
     const int64_t tauU_q = (int64_t)M * 65536 + j.Kq * D;
     const int64_t tauL_q = (int64_t)M * 65536 - j.Kq * D;
@@ -182,8 +215,28 @@ int excise_window(const Job &j, int64_t w) {
         store(j, s0 + i, out);
     }
     if (j.counts) j.counts[w] = flagged;
-    if (j.median) j.median[w] = M;
-    if (j.mad) j.mad[w] = D;
+}
+
+// Run f(w) for windows 0..nw-1 on nt threads (interleaved); returns the first non-OK status.
+template <class F>
+int for_windows(int64_t nw, int32_t nthreads, F f) {
+    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(nthreads, nw));
+    std::vector<int> status(nt, ORACLE_OK);
+    auto worker = [&](int t) {
+        for (int64_t w = t; w < nw; w += nt) {
+            const int s = f(w);
+            if (s != ORACLE_OK) status[t] = s;
+        }
+    };
+    if (nt == 1) {
+        worker(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t) th.emplace_back(worker, t);
+        for (auto &t : th) t.join();
+    }
+    for (int s : status)
+        if (s != ORACLE_OK) return s;
     return ORACLE_OK;
 }
 
@@ -239,24 +292,55 @@ int oracle_excise(const oracle_args *a) {
           a->seed, a->stream_id, a->mask, a->counts, a->median, a->mad};
     if (j.Kq < 1) return ORACLE_BAD_ARG;
     const int64_t nw = (a->len + a->W - 1) / a->W;
-    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(a->nthreads, nw));
-    std::vector<int> status(nt, ORACLE_OK);
-    auto worker = [&](int t) {
-        for (int64_t w = t; w < nw; w += nt) {
-            const int s = excise_window(j, w);
-            if (s != ORACLE_OK) status[t] = s;
-        }
-    };
-    if (nt == 1) {
-        worker(0);
-    } else {
-        std::vector<std::thread> th;
-        for (int t = 0; t < nt; ++t) th.emplace_back(worker, t);
-        for (auto &t : th) t.join();
-    }
-    for (int s : status)
-        if (s != ORACLE_OK) return s;
-    return ORACLE_OK;
+    return for_windows(nw, a->nthreads, [&](int64_t w) { return excise_window(j, w); });
+}
+
+// Median of MAD (Eq. 3): the dispersion of window j is the lower median of the MADs of the
+// k_mom successive windows ending at j, D_{j-k_mom+1} .. D_j; windows before the first one of
+// the stream do not exist, so early windows take the median of the MADs there are. The
+// thresholds (Eq. 1) are then set around the window's own median M_j with that dispersion, and
+// Eq. 2 and the replacement options apply unchanged. history holds the MADs of the n_history
+// windows just before x (oldest first, n_history <= k_mom - 1), so a stream excised in slices
+// equals the whole stream; mom (nullable) receives the dispersion used per window.
+int oracle_excise_mom(const oracle_args *a, int32_t k_mom, const int32_t *history, int64_t n_history,
+                      int32_t *mom) {
+    if (!a || !a->x || !a->z || (a->bits != 8 && a->bits != 12) || a->len < 1 || a->W < 1 ||
+        a->W > 65536 || a->abs0 < 0 || (a->abs0 % a->W) != 0 || !(a->n_sigma > 0.0) ||
+        a->mode < 0 || a->mode > 3 || k_mom < 1 || n_history < 0 || n_history > k_mom - 1 ||
+        (n_history > 0 && !history))
+        return ORACLE_BAD_ARG;
+    Job j{a->x, a->z, a->bits, a->len, a->W, a->abs0, k_q16(a->n_sigma), a->mode, a->const_value,
+          a->seed, a->stream_id, a->mask, a->counts, a->median, a->mad};
+    if (j.Kq < 1) return ORACLE_BAD_ARG;
+    const int64_t nw = (a->len + a->W - 1) / a->W;
+    // 1. M_j and D_j of every window
+    std::vector<int32_t> M(nw), D(n_history + nw);
+    for (int64_t i = 0; i < n_history; ++i) D[i] = history[i];
+    int st = for_windows(nw, a->nthreads, [&](int64_t w) {
+        std::vector<int32_t> x;
+        if (!window_samples(j, w, x)) return ORACLE_SAMPLE_RANGE;
+        window_stats(x, &M[w], &D[n_history + w]);
+        return ORACLE_OK;
+    });
+    if (st != ORACLE_OK) return st;
+    // 2. Eq. 3: M_m = M(D_{j-k+1}, ..., D_j), lower median, over the windows that exist
+    std::vector<int32_t> Mm(nw);
+    for_windows(nw, a->nthreads, [&](int64_t w) {
+        const int64_t end = n_history + w + 1;
+        const int64_t begin = std::max<int64_t>(0, end - k_mom);
+        Mm[w] = lower_median(std::vector<int32_t>(D.begin() + begin, D.begin() + end));
+        return ORACLE_OK;
+    });
+    // 3. Eq. 1 and Eq. 2 around M_j with dispersion M_m
+    return for_windows(nw, a->nthreads, [&](int64_t w) {
+        std::vector<int32_t> x;
+        window_samples(j, w, x);
+        apply_window(j, w, x, M[w], Mm[w]);
+        if (j.median) j.median[w] = M[w];
+        if (j.mad) j.mad[w] = D[n_history + w];
+        if (mom) mom[w] = Mm[w];
+        return ORACLE_OK;
+    });
 }
 
 }  // extern "C"

@@ -390,7 +390,7 @@ class _DevArray:
     """A raw device pointer seen as a tensor (zero-copy), through __cuda_array_interface__."""
 
     def __init__(self, ptr, n, typestr):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, True),
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
                                          "version": 2}
 
 
