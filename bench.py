@@ -43,7 +43,13 @@ def env_rank():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
-def workload_desc(nstreams, length):
+def workload_desc(nstreams, length, name="gwb60"):
+    if name == "twelve60":
+        return ("twelve60: %d streams x 2^25 12-bit samples (int16), window 8192, k 3.5, noise seed 7, "
+                "sigma 120, bursts 5e-3 x U{1..256}, drift 50 LSB (1 call per step)" % nstreams)
+    if name == "uneven60":
+        return ("uneven60: %d int8 streams of floor(2^U[22,27]) samples, windows 2^U{10..16}, k 3, noise "
+                "seed 7 (1 call per step)" % nstreams)
     return ("gwb60: %d streams x 2^%d int8 samples, window 16384, k {3,5} x {zero, const 1, clip, "
             "noise seed 7} (8 calls per step)" % (nstreams, length.bit_length() - 1))
 
@@ -135,19 +141,21 @@ def profiled_traffic():
     return int(m1.group(1)), "ncu"
 
 
-def cpu_oracle_sample(xs, variants, windows_per_stream, W):
+def cpu_oracle_sample(xs, variants, windows_per_stream, W, bits=8):
     """Run the oracle on the first windows_per_stream windows of every stream for every variant,
-    one stream per host core at a time; returns (samples, seconds, threads)."""
+    one stream per host core at a time; returns (samples, seconds, threads). W is one window
+    length or one per stream."""
     from concurrent.futures import ThreadPoolExecutor
 
     import oracle
     threads = os.cpu_count() or 1
-    parts = [x[: windows_per_stream * W] for x in xs]
+    Ws = list(W) if isinstance(W, (list, tuple)) else [W] * len(xs)
+    parts = [x[: windows_per_stream * Ws[i]] for i, x in enumerate(xs)]
 
     def one(args):
         v, i = args
-        oracle.excise(parts[i], W, v.k, v.mode, const=v.const, seed=v.seed, stream_id=i, threads=1,
-                      want=("z", "mask", "counts"))
+        oracle.excise(parts[i], Ws[i], v.k, v.mode, const=v.const, seed=v.seed, stream_id=i, bits=bits,
+                      threads=1, want=("z", "mask", "counts"))
         return parts[i].size
 
     jobs = [(v, i) for v in variants for i in range(len(parts))]
@@ -203,8 +211,16 @@ def run_ours(args):
     group = rdist.Group("nccl" if world > 1 else None, device=dev)
     barrier, max_over_ranks, sum_over_ranks = group.barrier, group.max, group.sum
 
-    W = 16384
-    w = workloads.gwb60(length=args.length, nstreams=args.streams)
+    if args.workload == "twelve60":
+        w = workloads.twelve60(nstreams=args.streams)
+    elif args.workload == "uneven60":
+        w = workloads.uneven60(nstreams=args.streams)
+    else:
+        w = workloads.gwb60(length=args.length, nstreams=args.streams)
+    bits = w.bits
+    esz = 1 if bits == 8 else 2
+    Ws = [st_.window for st_ in w.streams]
+    W = Ws[0]
     # each rank excises its own 60-stream batch (a different antenna set): weak scaling
     sids = rdist.stream_ids(rank, len(w.streams))
     t_gen = time.perf_counter()
@@ -214,17 +230,18 @@ def run_ours(args):
     lens = [x.size for x in xs]
     dev_in = [torch.from_numpy(x).to(dev) for x in xs]
     out = [torch.empty_like(t) for t in dev_in]
-    nwin = [-(-n // W) for n in lens]
-    masks = [torch.empty(nw * (W // 32), dtype=torch.int32, device=dev) for nw in nwin]
+    nwin = [-(-n // Ws[i]) for i, n in enumerate(lens)]
+    mwords = [nw * ((Ws[i] + 31) // 32) for i, nw in enumerate(nwin)]
+    masks = [torch.empty(mw, dtype=torch.int32, device=dev) for mw in mwords]
     counts = [torch.empty(nw, dtype=torch.int32, device=dev) for nw in nwin]
     samples_per_call = sum(lens)
     windows_per_call = sum(nwin)
     stream = torch.cuda.Stream(device=dev)
 
-    batched = [rfi.Plan(8, lens, [W] * S, v.k, v.mode, v.const, v.seed,
+    batched = [rfi.Plan(bits, lens, Ws, v.k, v.mode, v.const, v.seed,
                         rfi.RFI_PLAN_GRAPH | rfi.RFI_PLAN_AUTOTUNE, sids)
                for v in w.variants]
-    per_stream = [rfi.Plan(8, lens, [W] * S, v.k, v.mode, v.const, v.seed, rfi.RFI_PLAN_PER_STREAM, sids)
+    per_stream = [rfi.Plan(bits, lens, Ws, v.k, v.mode, v.const, v.seed, rfi.RFI_PLAN_PER_STREAM, sids)
                   for v in w.variants]
     info = batched[0].info()
 
@@ -274,20 +291,55 @@ def run_ours(args):
     ps_value = sum_over_ranks(samples_per_call * len(per_stream) * ps_steps) / (ps_ms * 1e-3) / 1e9
 
     # roofline of the persistent kernel: algorithmic bytes per launch / mean launch time
-    alg_bytes = samples_per_call * (2 + 1 / 8) + windows_per_call * 12
+    alg_bytes = samples_per_call * (2 * esz + 1 / 8) + windows_per_call * 12
     mean_call_s = statistics.mean(calls) * 1e-3
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / mean_call_s / 1e9
-    traffic, traffic_src = profiled_traffic()
+    traffic, traffic_src = profiled_traffic() if args.workload == "gwb60" else (None, "profiled on gwb60 only")
     ps_mean_s = statistics.mean(ps_calls) * 1e-3 / S   # per launch (one stream)
     ps_achieved = (alg_bytes / S) / ps_mean_s / 1e9
+
+    # Median of MAD (Eq. 3) in the GWB's MoM configuration: 4096-sample windows, the median of the
+    # last 4096 MADs, on the same device-resident streams (three kernels per call, CUDA graph)
+    mom = None
+    if not args.no_mom and args.workload == "gwb60":
+        WM, KM = 4096, 4096
+        mplan = rfi.Plan(8, lens, [WM] * S, 3.0, workloads.NOISE, 0, 7, rfi.RFI_PLAN_GRAPH, sids, mom_windows=KM)
+        nwm = [-(-n // WM) for n in lens]
+        mmask = [torch.empty(nw * (WM // 32), dtype=torch.int32, device=dev) for nw in nwm]
+        mcnt = [torch.empty(nw, dtype=torch.int32, device=dev) for nw in nwm]
+        msteps = max(1, min(args.steps, 10))
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                mplan.excise(dev_in, out, mmask, mcnt, stream)
+            stream.synchronize()
+            barrier()
+            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            for _ in range(msteps):
+                mplan.excise(dev_in, out, mmask, mcnt, stream)
+            m1.record(stream)
+            stream.synchronize()
+        mst, mtot = mplan.stats(stream=stream)
+        if mst != 0:
+            raise RuntimeError("MoM device status %s" % rfi.rfi_status_string(mst))
+        mom_ms = max_over_ranks(m0.elapsed_time(m1)) / msteps
+        mom_bytes = samples_per_call * (1 + 2 + 1 / 8) + sum(nwm) * 24
+        mom = {"value": sum_over_ranks(samples_per_call) / (mom_ms * 1e-3) / 1e9, "unit": UNIT,
+               "ms_per_call": mom_ms, "calls": msteps, "window": WM, "mom_windows": KM,
+               "variant": "k 3, noise seed 7", "launches_per_call": 3,
+               "achieved_gbs": mom_bytes / (mom_ms * 1e-3) / 1e9, "frac": mom_bytes / (mom_ms * 1e-3) / 1e9 / peak,
+               "bytes_rule": "per sample 1 read (estimation) + 1 read + 1 write + 1/8 mask (apply); "
+                             "per window 4 count + 8 M/D + 12 MAD/MoM traffic"}
+        mplan.close()
+        del mmask, mcnt
 
     # end to end through rfi_excise_host with pinned host buffers
     e2e = None
     if not args.no_e2e:
         h_in = [torch.from_numpy(x).pin_memory() for x in xs]
         h_out = [torch.empty_like(t).pin_memory() for t in h_in]
-        h_mask = [torch.empty(nw * (W // 32), dtype=torch.int32).pin_memory() for nw in nwin]
+        h_mask = [torch.empty(mw, dtype=torch.int32).pin_memory() for mw in mwords]
         h_cnt = [torch.empty(nw, dtype=torch.int32).pin_memory() for nw in nwin]
         e2e_steps = max(1, min(args.steps, args.e2e_steps))
         for p in batched[:1]:
@@ -300,8 +352,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         e2e_s = max_over_ranks(time.perf_counter() - t0)
-        h2d = samples_per_call * len(batched)
-        d2h = (samples_per_call + sum(m.numel() * 4 for m in h_mask) + windows_per_call * 4) * len(batched)
+        h2d = samples_per_call * esz * len(batched)
+        d2h = (samples_per_call * esz + sum(m.numel() * 4 for m in h_mask) + windows_per_call * 4) * len(batched)
         e2e = {"value": sum_over_ranks(samples_per_call * len(batched) * e2e_steps) / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                "path": "rfi_excise_host, pinned host buffers, 32 MiB chunks on 3 streams"}
@@ -310,7 +362,7 @@ def run_ours(args):
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        n, t, threads = cpu_oracle_sample(xs, w.variants, args.cpu_windows, W)
+        n, t, threads = cpu_oracle_sample(xs, w.variants, args.cpu_windows, Ws, bits)
         cpu = {"value": n / t / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "first %d windows of each of the %d streams, all 8 variants (%d samples, %.1f s)"
                          % (args.cpu_windows, S, n, t)}
@@ -321,16 +373,19 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-            "config": {"workload": workload_desc(S, args.length), "streams": S, "samples_per_stream": args.length,
-                       "window": W, "variants": len(batched),
+            "scaling": "weak", "vs_baseline": None, "dtype": "int8" if bits == 8 else "int16",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(S, args.length, args.workload), "streams": S,
+                       "samples_per_stream": args.length if args.workload == "gwb60" else None,
+                       "samples": samples_per_call,
+                       "window": W if len(set(Ws)) == 1 else "per stream", "variants": len(batched),
                        "form": "batched persistent kernel, CUDA graph, autotuned launch shape",
                        "launch_shape": {"consumer_warps": info.shape.consumer_warps, "stages": info.shape.stages,
                                         "ctas_per_sm": info.shape.ctas_per_sm,
                                         "stage_bytes": info.shape.stage_bytes,
                                         "dynamic_tiles": info.shape.dynamic_tiles, "groups": info.shape.groups,
                                         "grid": info.grid},
-                       "l2": "inputs (%d MiB per rank) larger than L2 (129 MB)" % (samples_per_call >> 20),
+                       "l2": "inputs (%d MiB per rank) larger than L2 (129 MB)" % ((samples_per_call * esz) >> 20),
                        "parallelism": "replicas (one 60-stream batch per GPU)", "feed_gen_s": round(t_gen, 2)},
             "per_stream": {"value": ps_value, "unit": UNIT, "ms_per_step": ps_ms / ps_steps, "steps": ps_steps,
                            "achieved_gbs": ps_achieved, "frac": ps_achieved / peak,
@@ -339,12 +394,202 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "traffic_source": traffic_src,
                          "algorithmic_bytes_per_launch": int(alg_bytes),
-                         "bytes_rule": "per sample 1 read + 1 write + 1/8 mask; per window 4 count + 8 M/D",
-                         "mean_launch_ms": statistics.mean(calls), "kernel": "persistent_kernel<8,mode,cw>"},
+                         "bytes_rule": "per sample 1 read + 1 write (%d B each) + 1/8 mask; per window 4 count + 8 M/D"
+                                       % esz,
+                         "mean_launch_ms": statistics.mean(calls),
+                         "kernel": "persistent_kernel<%d,mode,cw,g>" % bits},
             "cpu_baseline": cpu,
+            "mom": mom,
             "e2e": e2e,
             "gpu_launches": len(batched) * args.steps,
+            "gpu_launches_note": "persistent-kernel launches in the timed region of `value`",
             "clocks": clocks_b,
+        }
+        print(json.dumps(line), flush=True)
+    group.close()
+    return 0
+
+
+def serve_desc(nstreams, seconds, feed):
+    return ("serve60: %d int8 streams paced at 800 Msps each for %g s of stream time, window 16384, "
+            "k 3, noise seed 7; chunks log-uniform 64 KiB-16 MiB from a %s-resident feed; backfill "
+            "requests of 2^floor(U[20,28]) samples at Poisson rate 2/s; 40 GB budget"
+            % (nstreams, seconds, feed))
+
+
+def run_serve(args):
+    """The serving workload: real-time streams paced at 800 Msps plus backfill requests through
+    rfi_server_*; reports chunk latency (scheduled arrival to done), RTF and throughput."""
+    import heapq
+
+    import numpy as np
+    import torch
+
+    import paper_1710_08576_gb300 as rfi
+    import synth
+    from synth import workloads
+
+    from paper_1710_08576_gb300 import dist as rdist
+
+    rank, local, world = rdist.env_rank()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    group = rdist.Group("nccl" if world > 1 else None, device=dev)
+    W, RATE = 16384, 800e6
+    w = workloads.serve60(window=W, nstreams=args.streams)
+    v = w.variants[0]
+    S = len(w.streams)
+    sids = rdist.stream_ids(rank, S)
+    rng = np.random.default_rng(1234 + rank)
+    # the feed: a resident pool per stream that chunks are copied from (stands in for ADC/NIC DMA)
+    POOL, MAXC, MINC = 1 << 25, 1 << 24, 1 << 16
+    t_gen = time.perf_counter()
+    pool_h = np.empty((S, POOL), np.int8)
+    for i, (st_, sid) in enumerate(zip(w.streams, sids)):
+        synth.fill(st_.feed, sid, POOL, out=pool_h[i])
+    REQ_MAX = 1 << 28
+    req_src_h = synth.fill(w.streams[0].feed, 4000 + rank, REQ_MAX)
+    t_gen = time.perf_counter() - t_gen
+    if args.feed == "host":
+        pool = torch.from_numpy(pool_h).pin_memory()
+    else:
+        pool = torch.from_numpy(pool_h).to(dev)
+    del pool_h
+    nslots = 4
+    req_src = torch.from_numpy(req_src_h).to(dev)
+    req_out = [torch.empty(REQ_MAX, dtype=torch.int8, device=dev) for _ in range(nslots)]
+    req_mask = [torch.empty(REQ_MAX // 32, dtype=torch.int32, device=dev) for _ in range(nslots)]
+    req_cnt = [torch.empty(REQ_MAX // W, dtype=torch.int32, device=dev) for _ in range(nslots)]
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):  # loads the kernel and warms the allocator paths
+        warm = rfi.Server(8, [W], 4 * W, v.k, v.mode, v.const, v.seed, 1 << 28, 1, 0)
+        rfi.check(warm.push(0, pool.data_ptr(), 2 * W, on_device=(args.feed == "device"))[0], "push")
+        warm.drain()
+        warm.close()
+    srv = rfi.Server(8, [W] * S, 1 << 26, v.k, v.mode, v.const, v.seed, 40 * 10 ** 9, nslots, 1024,
+                     stream_id=sids)
+    T = args.serve_seconds
+    # arrivals: per stream, chunk sizes log-uniform; a chunk arrives when its last sample does
+    heap = []
+    produced = [0] * S
+    sched_end = [0] * S
+
+    def next_chunk(s):
+        n = int(np.exp(rng.uniform(np.log(MINC), np.log(MAXC))))
+        n = min(n, int(T * RATE) - sched_end[s])
+        if n <= 0:
+            return
+        sched_end[s] += n
+        heapq.heappush(heap, (sched_end[s] / RATE, s, n))
+
+    for s in range(S):
+        next_chunk(s)
+    req_t = list(np.cumsum(rng.exponential(0.5, size=int(4 * T) + 8)))
+    req_t = [t for t in req_t if t < T]
+    req_free = list(range(nslots))
+    req_live = {}   # ticket -> slot
+    lag_of = {}     # chunk ticket -> host lag (s) between scheduled arrival and push
+    req_lag = {}    # request ticket -> host lag (s) between scheduled arrival and submit
+    stalls = req_stalls = nreq = 0
+    req_samples = 0
+    ptr0 = pool.data_ptr()
+    clocks = ClockSampler(local)
+    group.barrier()
+    clocks.start()
+    t0 = time.perf_counter()
+    last_release = 0.0
+    while heap or req_t:
+        now = time.perf_counter() - t0
+        while heap and heap[0][0] <= now:
+            ta, s, n = heap[0]
+            src = ptr0 + s * POOL + (produced[s] % MAXC)
+            st, tk = srv.push(s, src, n, on_device=(args.feed == "device"))
+            if st == rfi.RFI_ERR_BUSY:
+                stalls += 1
+                break
+            rfi.check(st, "push")
+            heapq.heappop(heap)
+            lag_of[tk] = (time.perf_counter() - t0) - ta
+            produced[s] += n
+            next_chunk(s)
+        while req_t and req_t[0] <= now and req_free:
+            size = 1 << int(rng.integers(20, 29))
+            slot = req_free.pop()
+            st, tk = srv.submit(req_src, req_out[slot], W, 5000 + nreq + 1000 * rank, 0, mask=req_mask[slot],
+                                counts=req_cnt[slot], on_device=True, n=size)
+            if st == rfi.RFI_ERR_BUSY:
+                req_free.append(slot)
+                req_stalls += 1
+                break
+            rfi.check(st, "submit")
+            req_lag[tk] = now - req_t[0]
+            req_t.pop(0)
+            req_live[tk] = slot
+            req_samples += size
+            nreq += 1
+        srv.step()
+        for tk in list(req_live):
+            if srv.poll(tk)[0]:
+                req_free.append(req_live.pop(tk))
+        if now - last_release > 1e-3:
+            for s in range(S):
+                _, c, r = srv.position(s)
+                if c > r:
+                    rfi.check(srv.release(s, c), "release")
+            last_release = now
+        nxt = heap[0][0] if heap else T
+        wait = nxt - (time.perf_counter() - t0)
+        if wait > 2e-4:
+            time.sleep(min(wait, 5e-4))
+    for s in range(S):
+        srv.flush(s)
+    srv.drain()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = srv.stats()
+    tickets, lats = srv.take_latencies()
+    srv.close()
+    if st.device_status != 0:
+        raise RuntimeError("device status %s" % rfi.rfi_status_string(st.device_status))
+    chunk_tot, req_tot = [], []
+    for tk, lat in zip(tickets, lats):
+        if tk in lag_of:
+            chunk_tot.append(lat + 1e6 * max(0.0, lag_of[tk]))
+        elif tk in req_lag:
+            req_tot.append(lat + 1e6 * max(0.0, req_lag[tk]))
+    stream_samples = sum(produced)
+    stream_time = T
+    p = lambda a, q: float(np.percentile(np.asarray(a), q)) if a else None  # noqa: E731
+    value = group.sum(stream_samples + req_samples) / group.max(wall) / 1e9
+    if rank == 0:
+        line = {
+            "metric": "serving: chunk latency p50/p99 (scheduled arrival to done), RTF, throughput",
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int8", "data": "synthetic",
+            "config": {"workload": serve_desc(S, T, args.feed), "streams": S, "window": W,
+                       "ring_samples": 1 << 26, "budget_bytes": 40 * 10 ** 9,
+                       "parallelism": "replicas (one 60-stream set per GPU)", "feed_gen_s": round(t_gen, 2)},
+            "serve": {"stream_seconds": stream_time, "wall_seconds": wall,
+                      "rtf": st.gpu_busy_seconds / stream_time,
+                      "gpu_busy_seconds": st.gpu_busy_seconds, "passes": st.passes,
+                      "chunks": st.chunks_done, "stream_samples": stream_samples,
+                      "requests": st.requests_done, "request_samples": req_samples,
+                      "push_stalls": stalls, "request_stalls": req_stalls,
+                      "chunk_latency_us": {"p50": p(chunk_tot, 50), "p99": p(chunk_tot, 99),
+                                           "max": max(chunk_tot) if chunk_tot else None},
+                      "chunk_device_latency_us": {"p50": st.chunk_latency_p50_us, "p99": st.chunk_latency_p99_us,
+                                                  "max": st.chunk_latency_max_us},
+                      "request_latency_us": {"p50": p(req_tot, 50), "p99": p(req_tot, 99)},
+                      "request_device_latency_us": {"p50": st.request_latency_p50_us,
+                                                    "p99": st.request_latency_p99_us},
+                      "host_lag_us": {"p50": p([1e6 * v for v in lag_of.values()], 50),
+                                      "p99": p([1e6 * v for v in lag_of.values()], 99)},
+                      "gsps_in_passes": (stream_samples + req_samples) / max(st.gpu_busy_seconds, 1e-9) / 1e9,
+                      "arena_peak_bytes": st.arena_peak_bytes},
+            "gpu_launches": int(st.passes) * 2,
+            "clocks": clk,
         }
         print(json.dumps(line), flush=True)
     group.close()
@@ -364,10 +609,16 @@ def main():
     ap.add_argument("--cpu-windows", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-mom", action="store_true")
+    ap.add_argument("--workload", choices=["gwb60", "twelve60", "uneven60", "serve60"], default="gwb60")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--feed", choices=["device", "host"], default="device")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    return run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_serve(args) if args.workload == "serve60" else run_ours(args)
 
 
 if __name__ == "__main__":

@@ -88,6 +88,11 @@ typedef enum rfi_mode {
 #define RFI_PLAN_BATCHED 0x2u     /* one persistent launch over all windows (default) */
 #define RFI_PLAN_GRAPH 0x4u       /* batched launch replayed from a CUDA graph */
 #define RFI_PLAN_AUTOTUNE 0x8u    /* time candidate launch shapes at create, keep the fastest */
+#define RFI_PLAN_POWER 0x10u      /* also sum x^2 and z^2 over every window (the detected power of
+                                     the unfiltered and filtered signal, rfi_stats_power), for
+                                     the improvement metric of Section III-A. Batched form and
+                                     per-window MAD only (RFI_ERR_UNSUPPORTED otherwise); fixed
+                                     launch shape as for mom_windows >= 2 */
 #define RFI_PLAN_INJECT_TIMEOUT 0x100u /* test hook: CTA 0 waits on a barrier nothing arrives
                                           on (bounded by 1 ms), latching RFI_ERR_TIMEOUT */
 
@@ -115,6 +120,14 @@ typedef struct rfi_plan_desc {
     uint64_t seed;                /* RFI_REPLACE_NOISE Philox key */
     uint32_t flags;               /* RFI_PLAN_* */
     const rfi_launch_shape *shape;/* NULL: autotuned or default shape */
+    int32_t mom_windows;          /* Median of MAD (Section II-D, Eq. 3): 0 or 1 = each window's
+                                     own MAD sets its thresholds; k >= 2 (<= 2^20) = the lower
+                                     median of the MADs of the k windows ending at the window
+                                     (fewer at a stream's start) does, around the window's own
+                                     median. k >= 2 needs the batched form: RFI_PLAN_PER_STREAM
+                                     and rfi_excise_host return RFI_ERR_UNSUPPORTED; the launch
+                                     shape is fixed (one group of 4 or 8 consumer warps) and
+                                     RFI_PLAN_AUTOTUNE has no effect. */
 } rfi_plan_desc;
 
 typedef struct rfi_plan_s *rfi_plan_t;
@@ -161,6 +174,29 @@ RFI_API rfi_status rfi_excise_host(rfi_plan_t plan, const void *const *in, void 
  * RFI_ERR_TIMEOUT) or a call error. */
 RFI_API rfi_status rfi_stats(rfi_plan_t plan, int32_t *const *median, int32_t *const *mad,
                      rfi_totals *totals, void *stream);
+
+/* Median-of-MAD plans (mom_windows >= 2): the dispersion each window of the last rfi_excise
+ * used, the lower median of the MADs of the mom_windows windows ending at it (Eq. 3), into
+ * caller device arrays of nwin(s) int32 (array pointer or element may be NULL). Asynchronous
+ * on `stream`. RFI_ERR_UNSUPPORTED for other plans. */
+RFI_API rfi_status rfi_stats_mom(rfi_plan_t plan, int32_t *const *mom, void *stream);
+
+/* RFI_PLAN_POWER plans: the detected power of every window of the last rfi_excise, two uint64
+ * per window {sum of x^2 over its input samples, sum of z^2 over its output samples}, into
+ * caller device arrays of 2 * nwin(s) (array pointer or element may be NULL). Asynchronous on
+ * `stream`. RFI_ERR_UNSUPPORTED for other plans. */
+RFI_API rfi_status rfi_stats_power(rfi_plan_t plan, uint64_t *const *power, void *stream);
+
+/* The improvement metric of Section III-A, on the host, from one stream's per-window power as
+ * rfi_stats_power writes it (host copy, 2 * nwin uint64): the power of windows_per_point
+ * consecutive windows makes one point of the detected-power series; the points are cut into
+ * blocks of points_per_block (a partial block is dropped); each block gives mean / RMS
+ * deviation about its mean (blocks with zero deviation are left out), averaged over the blocks
+ * into S_U (input) and S_F (output); *db = 10 log10(S_F / S_U), positive when excision improves
+ * the series. RFI_ERR_INVALID_ARG without a complete block on both sides. */
+RFI_API rfi_status rfi_improvement_db(const uint64_t *power, int64_t nwin, int32_t windows_per_point,
+                                      int32_t points_per_block, double *db, double *s_unfiltered,
+                                      double *s_filtered);
 
 /* Describe the plan (Kq, sizes, launch shape). */
 RFI_API rfi_status rfi_plan_get_info(rfi_plan_t plan, rfi_plan_info *info);
@@ -212,8 +248,10 @@ RFI_API rfi_status rfi_excise_noalloc(const rfi_plan_desc *desc, const void *con
  * every complete window that has arrived on every ring plus a bounded slice of every admitted
  * request, as long as fewer than two passes are in flight; work that arrives while a pass runs
  * joins the next one. rfi_server_poll reports whether a chunk or request is done and its latency
- * (push/submit to completion of its last window, on the device clock; a host request's also
- * covers the copy of its results back). rfi_server_read copies
+ * on the device clock, from the push or submit call to the end of the pass that excised its last
+ * window; a host request's also covers the copy of its results back. A chunk is done when every
+ * window that ends inside it is excised (a trailing partial window is completed by the next
+ * chunk of the stream, or by the flush, and is counted with that one). rfi_server_read copies
  * excised output of a stream out of the ring and may release it. Output equals the plan path on
  * the whole stream: windows are aligned to absolute multiples of W_s and the digital noise is
  * keyed by the absolute sample index, so chunking, batching and the mix of concurrent work do

@@ -1,5 +1,5 @@
-"""CPU oracle for windowed median/MAD RFI excision (Section II-D, Eq. 1 and Eq. 2) and its
-Median-of-MAD variant (Eq. 3).
+"""CPU oracle for windowed median/MAD RFI excision (Section II-D, Eq. 1 and Eq. 2), its
+Median-of-MAD variant (Eq. 3), and the improvement metric of Section III-A.
 
 TEST INFRASTRUCTURE: only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
 baseline leg may import this package. The definition it computes, and every reading it takes
@@ -111,6 +111,47 @@ def excise_mom(x: np.ndarray, W: int, k: float, mode: int, k_mom: int, const: in
                                                 p(hist) if hist.size else None, int(hist.size),
                                                 p(res["mom"])))
     return res
+
+
+def window_power(x: np.ndarray, W: int) -> np.ndarray:
+    """Detected power of each data window: the sum of x_i^2 over its samples (int64), the
+    per-window point of the power series the improvement metric is computed on."""
+    x = np.ascontiguousarray(x).astype(np.int64)
+    nw = -(-x.size // W)
+    p = np.zeros(nw, np.int64)
+    for w in range(nw):
+        seg = x[w * W:(w + 1) * W]
+        p[w] = int(np.dot(seg, seg))
+    return p
+
+
+def mean_to_rms(power: np.ndarray, windows_per_point: int = 1, points_per_block: int = 64) -> float:
+    """Average mean-to-RMS ratio of a detected-power series (Section III-A): the per-window
+    powers are summed into points of windows_per_point windows; the points are cut into blocks
+    of points_per_block; each block gives mean / RMS deviation about its mean; the blocks'
+    ratios are averaged. Blocks of zero RMS deviation are left out; a partial block is dropped."""
+    p = np.asarray(power, dtype=np.float64)
+    npt = p.size // windows_per_point
+    pts = p[:npt * windows_per_point].reshape(npt, windows_per_point).sum(axis=1)
+    nb = npt // points_per_block
+    ratios = []
+    for b in range(nb):
+        blk = pts[b * points_per_block:(b + 1) * points_per_block]
+        mean = blk.sum() / blk.size
+        rms = np.sqrt(((blk - mean) ** 2).sum() / blk.size)
+        if rms > 0:
+            ratios.append(mean / rms)
+    return float(np.mean(ratios)) if ratios else float("nan")
+
+
+def improvement_db(power_unfiltered, power_filtered, windows_per_point: int = 1, points_per_block: int = 64):
+    """The improvement metric of Section III-A from the per-window detected power of the
+    unfiltered and the filtered signal: 10 log10 of the ratio of their average mean-to-RMS
+    ratios, taken as S_F / S_U so that a positive value is an improvement. Returns
+    (dB, S_U, S_F)."""
+    su = mean_to_rms(power_unfiltered, windows_per_point, points_per_block)
+    sf = mean_to_rms(power_filtered, windows_per_point, points_per_block)
+    return 10.0 * np.log10(sf / su), su, sf
 
 
 def mask_words(W: int, n_windows: int) -> int:

@@ -28,6 +28,7 @@ RFI_PLAN_PER_STREAM = 0x1
 RFI_PLAN_BATCHED = 0x2
 RFI_PLAN_GRAPH = 0x4
 RFI_PLAN_AUTOTUNE = 0x8
+RFI_PLAN_POWER = 0x10
 RFI_PLAN_INJECT_TIMEOUT = 0x100
 
 
@@ -44,7 +45,8 @@ class RfiPlanDesc(ctypes.Structure):
                 ("window_len", ctypes.POINTER(ctypes.c_int32)),
                 ("stream_id", ctypes.POINTER(ctypes.c_uint32)), ("k", ctypes.c_double),
                 ("mode", ctypes.c_int32), ("const_value", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("flags", ctypes.c_uint32), ("shape", ctypes.POINTER(RfiLaunchShape))]
+                ("flags", ctypes.c_uint32), ("shape", ctypes.POINTER(RfiLaunchShape)),
+                ("mom_windows", ctypes.c_int32)]
 
 
 class RfiTotals(ctypes.Structure):
@@ -105,6 +107,11 @@ def _load():
         "rfi_excise": (ctypes.c_int, [_P, _PP, _PP, _PP, _PP, _P]),
         "rfi_excise_host": (ctypes.c_int, [_P, _PP, _PP, _PP, _PP, _P]),
         "rfi_stats": (ctypes.c_int, [_P, _PP, _PP, ctypes.POINTER(RfiTotals), _P]),
+        "rfi_stats_mom": (ctypes.c_int, [_P, _PP, _P]),
+        "rfi_stats_power": (ctypes.c_int, [_P, _PP, _P]),
+        "rfi_improvement_db": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "rfi_plan_get_info": (ctypes.c_int, [_P, ctypes.POINTER(RfiPlanInfo)]),
         "rfi_excise_noalloc": (ctypes.c_int, [ctypes.POINTER(RfiPlanDesc), _PP, _PP, _PP, _PP, _PP, _PP,
                                               ctypes.POINTER(RfiTotals), _P]),
@@ -176,7 +183,7 @@ def _stream(stream) -> int:
 
 
 def make_desc(bits, stream_len, window_len, k, mode, const_value=0, seed=0, flags=0, stream_id=None,
-              shape=None):
+              shape=None, mom_windows=0):
     n = len(stream_len)
     keep = []
     lens = (ctypes.c_int64 * n)(*[int(v) for v in stream_len])
@@ -193,7 +200,7 @@ def make_desc(bits, stream_len, window_len, k, mode, const_value=0, seed=0, flag
         shp = ctypes.pointer(shape)
         keep.append(shape)
     d = RfiPlanDesc(int(bits), n, lens, wins, sid, float(k), int(mode), int(const_value), int(seed),
-                    int(flags), shp)
+                    int(flags), shp, int(mom_windows))
     d._keep = keep
     return d
 
@@ -331,6 +338,18 @@ def rfi_server_destroy(server):
     return LIB.rfi_server_destroy(server)
 
 
+def rfi_improvement_db(power, windows_per_point=1, points_per_block=64):
+    """The improvement metric (Section III-A) of one stream's interleaved per-window power
+    (a host numpy array of 2 * nwin uint64/int64). Returns (status, dB, S_U, S_F)."""
+    import numpy as np
+    p = np.ascontiguousarray(power).view(np.uint64)
+    db, su, sf = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = LIB.rfi_improvement_db(p.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), p.size // 2,
+                                int(windows_per_point), int(points_per_block), ctypes.byref(db),
+                                ctypes.byref(su), ctypes.byref(sf))
+    return st, db.value, su.value, sf.value
+
+
 # ---------------------------------------------------------------- convenience wrapper
 class RfiError(RuntimeError):
     def __init__(self, status: int, what: str):
@@ -347,9 +366,9 @@ class Plan:
     """Owns one rfi_plan_t. Buffers are torch tensors (or raw device pointers)."""
 
     def __init__(self, bits, stream_len, window_len, k, mode, const_value=0, seed=0, flags=0,
-                 stream_id=None, shape=None):
+                 stream_id=None, shape=None, mom_windows=0):
         self.desc = make_desc(bits, stream_len, window_len, k, mode, const_value, seed, flags,
-                              stream_id, shape)
+                              stream_id, shape, mom_windows)
         st, h = rfi_plan_create(self.desc)
         check(st, "rfi_plan_create")
         self.handle = h
@@ -373,6 +392,17 @@ class Plan:
     def stats(self, medians=None, mads=None, stream=None):
         st, t = rfi_stats(self.handle, medians, mads, stream)
         return st, t
+
+    def stats_power(self, powers, stream=None):
+        """RFI_PLAN_POWER plans: copy {sum x^2, sum z^2} per window into the device arrays `powers`
+        (2 * nwin uint64, or int64 tensors of that size)."""
+        pa = _ptr_array(powers)
+        check(LIB.rfi_stats_power(self.handle, pa[0], _stream(stream)), "rfi_stats_power")
+
+    def stats_mom(self, moms, stream=None):
+        """Median-of-MAD plans: copy each window's MoM (Eq. 3) into the device arrays `moms`."""
+        pa = _ptr_array(moms)
+        check(LIB.rfi_stats_mom(self.handle, pa[0], _stream(stream)), "rfi_stats_mom")
 
     def info(self) -> RfiPlanInfo:
         st, i = rfi_plan_get_info(self.handle)
@@ -424,8 +454,9 @@ class Server:
         n = samples.numel() if n is None else n
         return rfi_server_push(self.handle, stream, samples, n, on_device)
 
-    def submit(self, inp, out, window_len, stream_id=0, abs0=0, mask=None, counts=None, on_device=True):
-        n = inp.numel() if hasattr(inp, "numel") else inp.size
+    def submit(self, inp, out, window_len, stream_id=0, abs0=0, mask=None, counts=None, on_device=True, n=None):
+        if n is None:
+            n = inp.numel() if hasattr(inp, "numel") else inp.size
         req = RfiRequestDesc(_ptr(inp), _ptr(out), _ptr(mask) or None, _ptr(counts) or None, int(n),
                              int(window_len), int(stream_id), int(abs0), int(bool(on_device)))
         return rfi_server_submit(self.handle, req)

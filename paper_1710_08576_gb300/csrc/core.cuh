@@ -26,9 +26,11 @@
 // difference, a three-operation byte compare against t, a byte permute that replicates each
 // byte's flag bit into 0x00/0xFF, and a byte dot product that packs the flags into mask bits.
 //
-// Digital-noise replacement is compacted per warp: each lane keeps the flag masks of four
-// rounds of chunks, then the warp numbers the flagged samples and all 32 lanes evaluate Philox
-// for 32 of them at a time, so no lane idles while another one runs a long noise loop.
+// Digital-noise replacement is deferred and shared out: the replace pass writes the flagged
+// samples' positions into a per-group list in shared memory, and after one more group barrier
+// all threads of the group evaluate Philox for the list, so neither a lane nor a warp idles
+// while another one runs a long noise loop. A window whose list would overflow hands the rest
+// of its flagged samples to a per-warp path that numbers them across the warp.
 
 #pragma once
 
@@ -211,6 +213,8 @@ struct Ctl {
     uint32_t count[2];   // flagged samples, by window parity
     uint32_t done[2];    // warps finished with the window, by window parity
     uint32_t err[2];     // 12-bit range error seen in the window, by window parity
+    uint32_t ncount[2];  // digital-noise list entries, by window parity
+    unsigned long long pw[2][2];  // power-metered excision: {sum x^2, sum z^2}, by window parity
     uint32_t abort;      // set when any warp gave up on a bounded wait
     int32_t mb;          // median bin of the current window (written by its owner thread)
     unsigned long long flagged;  // group total
@@ -231,6 +235,17 @@ struct Shm {
     Ctl *ctl;
     int ncopies;         // 12-bit only
     int bar_id;          // named barrier of this consumer group
+    uint16_t *nlist;     // digital noise: positions of the window's flagged samples (or null)
+};
+
+// Capacity of the digital-noise list and the mark of an entry that was handed to the warp path.
+constexpr int kNoiseList = 4096;
+constexpr uint16_t kNoiseSkip = 0xFFFFu;
+
+// Per-thread sums of x^2 and z^2 of the power-metered excision. A thread sees at most
+// 65536 / 128 samples of a window, each below 2^22, so 32 bits hold its sums.
+struct Pow {
+    uint32_t x, z;
 };
 
 // One window to process.
@@ -450,12 +465,44 @@ __device__ __forceinline__ int32_t sat_to(int64_t v, int32_t lo, int32_t hi) {
     return v < lo ? lo : (v > hi ? hi : static_cast<int32_t>(v));
 }
 
+// Threshold and replacement values of a window with median M and dispersion D (Eq. 1; D is the
+// window's MAD, or the median of MADs of Eq. 3).
+template <int BITS>
+__device__ __forceinline__ RepShared make_rep(int32_t M, int32_t d, int64_t kq, int32_t cval) {
+    constexpr int SPAN = Geo<BITS>::kHi - Geo<BITS>::kLo;
+    RepShared r;
+    r.M = M;
+    r.D = d;
+    const int64_t kd = kq * static_cast<int64_t>(d);
+    const int64_t t = (kd + 65535) >> 16;
+    const int64_t c = kd >> 16;
+    r.t = static_cast<int32_t>(t < SPAN + 1 ? t : SPAN + 1);
+    r.hiv = sat_to(static_cast<int64_t>(r.M) + c, Geo<BITS>::kLo, Geo<BITS>::kHi);
+    r.lov = sat_to(static_cast<int64_t>(r.M) - c, Geo<BITS>::kLo, Geo<BITS>::kHi);
+    r.sigq = 97164u * static_cast<uint32_t>(d);
+    r.active = (d > 0 && t <= SPAN) ? 1u : 0u;  // |x - M| never exceeds the sample span
+    r.pad = 0u;
+    if (BITS == 8) {
+        const uint32_t tt = static_cast<uint32_t>(r.t > 255 ? 255 : r.t);
+        const uint32_t ub = static_cast<uint32_t>(r.M + 129);  // smallest biased value above M
+        r.mb4 = static_cast<uint32_t>(r.M + 128) * 0x01010101u;
+        r.tlo7 = (tt & 0x7Fu) * 0x01010101u;
+        r.tsmall = tt < 128u ? ~0u : 0u;
+        r.c4 = (static_cast<uint32_t>(cval) & 0xFFu) * 0x01010101u;
+        r.hi4 = (static_cast<uint32_t>(r.hiv) & 0xFFu) * 0x01010101u;
+        r.lo4 = (static_cast<uint32_t>(r.lov) & 0xFFu) * 0x01010101u;
+        r.ulo7 = (ub & 0x7Fu) * 0x01010101u;
+        r.usmall = ub < 128u ? ~0u : 0u;
+        r.unone = ub > 255u ? 1u : 0u;
+    }
+    return r;
+}
+
 // One warp: lower median bin, then the MAD, then the threshold and replacement values, written
 // to the shared control block.
 template <int BITS>
 __device__ __forceinline__ void phase_search(const Shm &sm, int n, int lane, int64_t kq, int32_t cval) {
     constexpr int B = Geo<BITS>::kBins;
-    constexpr int SPAN = Geo<BITS>::kHi - Geo<BITS>::kLo;
     const uint32_t *cum = sm.cum;
     const uint32_t half = static_cast<uint32_t>((n + 1) >> 1);
     const int mb = sm.ctl->mb;  // found by its owner thread during the scan
@@ -465,34 +512,7 @@ __device__ __forceinline__ void phase_search(const Shm &sm, int n, int lane, int
         const uint32_t f = cum[pad32(hi)] - (lo >= 0 ? cum[pad32(lo)] : 0u);
         return f >= half;
     });
-    if (lane == 0) {
-        RepShared r;
-        r.M = mb - Geo<BITS>::kOffset;
-        r.D = d;
-        const int64_t kd = kq * static_cast<int64_t>(d);
-        const int64_t t = (kd + 65535) >> 16;
-        const int64_t c = kd >> 16;
-        r.t = static_cast<int32_t>(t < SPAN + 1 ? t : SPAN + 1);
-        r.hiv = sat_to(static_cast<int64_t>(r.M) + c, Geo<BITS>::kLo, Geo<BITS>::kHi);
-        r.lov = sat_to(static_cast<int64_t>(r.M) - c, Geo<BITS>::kLo, Geo<BITS>::kHi);
-        r.sigq = 97164u * static_cast<uint32_t>(d);
-        r.active = (d > 0 && t <= SPAN) ? 1u : 0u;  // |x - M| never exceeds the sample span
-        r.pad = 0u;
-        if (BITS == 8) {
-            const uint32_t tt = static_cast<uint32_t>(r.t > 255 ? 255 : r.t);
-            const uint32_t ub = static_cast<uint32_t>(r.M + 129);  // smallest biased value above M
-            r.mb4 = static_cast<uint32_t>(r.M + 128) * 0x01010101u;
-            r.tlo7 = (tt & 0x7Fu) * 0x01010101u;
-            r.tsmall = tt < 128u ? ~0u : 0u;
-            r.c4 = (static_cast<uint32_t>(cval) & 0xFFu) * 0x01010101u;
-            r.hi4 = (static_cast<uint32_t>(r.hiv) & 0xFFu) * 0x01010101u;
-            r.lo4 = (static_cast<uint32_t>(r.lov) & 0xFFu) * 0x01010101u;
-            r.ulo7 = (ub & 0x7Fu) * 0x01010101u;
-            r.usmall = ub < 128u ? ~0u : 0u;
-            r.unone = ub > 255u ? 1u : 0u;
-        }
-        sm.ctl->rep = r;
-    }
+    if (lane == 0) sm.ctl->rep = make_rep<BITS>(mb - Geo<BITS>::kOffset, d, kq, cval);
 }
 
 __device__ __forceinline__ Rep load_rep(const Ctl *ctl) {
@@ -577,9 +597,9 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int j) {
 // that owns it and a popcount search for its bit, and all 32 lanes evaluate Philox together.
 // The stores go straight to the output; they follow the chunks' own stores in warp order
 // (__syncwarp before the call).
-template <int BITS, int T>
+template <int BITS, int T, bool PW>
 __device__ __forceinline__ void noise_batch(const Win &w, const Rep &r, const Params &p, int lane, int c0,
-                                            uint64_t nb) {
+                                            uint64_t nb, Pow &pw) {
     constexpr int CS = Geo<BITS>::kChunkSamples;
     const uint32_t lo = static_cast<uint32_t>(nb), hi = static_cast<uint32_t>(nb >> 32);
     const uint32_t cnt = __popc(lo) + __popc(hi);
@@ -614,36 +634,75 @@ __device__ __forceinline__ void noise_batch(const Win &w, const Rep &r, const Pa
             const int32_t z = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pos, Geo<BITS>::kLo, Geo<BITS>::kHi);
             if (BITS == 8) w.out[pos] = static_cast<uint8_t>(z);
             else reinterpret_cast<int16_t *>(w.out)[pos] = static_cast<int16_t>(z);
+            if (PW) pw.z += static_cast<uint32_t>(z * z);
         }
     }
 }
 
-// Collects a round's flag masks for noise_batch; every fourth round (and at the end) it runs
-// the batch. nb/nk/c0 are the lane's batch state (nk warp-uniform).
-template <int BITS, int T>
-__device__ __forceinline__ void noise_collect(const Win &w, const Rep &r, const Params &p, int lane, int c,
-                                              uint32_t bits, uint64_t &nb, int &nk, int &c0) {
-    if (nk == 0) c0 = c;
-    nb |= static_cast<uint64_t>(bits) << (16 * nk);
-    if (++nk == 4) {
-        __syncwarp();
-        if (__any_sync(0xFFFFFFFFu, nb != 0)) noise_batch<BITS, T>(w, r, p, lane, c0, nb);
-        nb = 0;
-        nk = 0;
+// Digital noise, replace pass: the warp numbers its flagged samples of this round, reserves that
+// many list entries with one shared atomic, and each lane writes its positions. Windows of
+// 65536 samples (position 65535 would equal the skip mark) and rounds that do not fit in the
+// list take the per-warp path at once; list entries reserved beyond the written ones are
+// marked skipped. Called by all lanes of the warp with the round's chunk c and flag bits.
+template <int BITS, int T, bool PW>
+__device__ __forceinline__ void noise_append(const Shm &sm, const Win &w, const Rep &r, const Params &p, int lane,
+                                             int c, uint32_t bits, int par, Pow &pw) {
+    constexpr int CS = Geo<BITS>::kChunkSamples;
+    if (!__any_sync(0xFFFFFFFFu, bits != 0u)) return;
+    const uint32_t cnt = __popc(bits);
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    const bool listed = sm.nlist != nullptr && w.n < 65536;
+    uint32_t base = kNoiseList;
+    if (listed && lane == 31) base = atomicAdd(&sm.ctl->ncount[par], total);
+    base = __shfl_sync(0xFFFFFFFFu, base, 31);
+    if (base + total <= static_cast<uint32_t>(kNoiseList)) {
+        uint32_t off = base + inc - cnt;
+        for (uint32_t m = bits; m; m &= m - 1u) sm.nlist[off++] = static_cast<uint16_t>(c * CS + __ffs(m) - 1);
+        return;
+    }
+    for (uint32_t i = base + lane; i < static_cast<uint32_t>(kNoiseList); i += 32) sm.nlist[i] = kNoiseSkip;
+    __syncwarp();  // the round's chunk stores come first
+    noise_batch<BITS, T, PW>(w, r, p, lane, c, static_cast<uint64_t>(bits), pw);
+}
+
+// Digital noise, after the group barrier that follows the replace pass: every thread of the
+// group evaluates Philox for a share of the list and stores the value over the chunk's output.
+template <int BITS, int T, bool PW>
+__device__ __forceinline__ void noise_list(const Shm &sm, const Win &w, const Rep &r, const Params &p, int tid,
+                                           int par, Pow &pw) {
+    if (sm.nlist == nullptr) return;
+    const uint32_t n = min(sm.ctl->ncount[par], static_cast<uint32_t>(kNoiseList));
+    for (uint32_t i = static_cast<uint32_t>(tid); i < n; i += T) {
+        const uint32_t pos = sm.nlist[i];
+        if (pos == kNoiseSkip) continue;
+        const int32_t z = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pos, Geo<BITS>::kLo, Geo<BITS>::kHi);
+        if (BITS == 8) w.out[pos] = static_cast<uint8_t>(z);
+        else reinterpret_cast<int16_t *>(w.out)[pos] = static_cast<int16_t>(z);
+        if (PW) pw.z += static_cast<uint32_t>(z * z);
     }
 }
 
-template <int BITS, int MODE, int T>
+// Sum of squares of the bytes of w kept by keep (0xFF per kept byte), as signed int8 samples.
+__device__ __forceinline__ uint32_t sq4(uint32_t w, uint32_t keep) {
+    const int32_t v = static_cast<int32_t>(w & keep);
+    return static_cast<uint32_t>(__dp4a(v, v, 0));
+}
+
+template <int BITS, int MODE, int T, bool PW>
 __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, const Rep &r, const Params &p,
-                                                  int tid) {
+                                                  int tid, int par, Pow &pw) {
     constexpr int BPS = Geo<BITS>::kBps;
     const int lane = tid & 31, warp = tid >> 5;
     const int nbytes = w.n * BPS;
     const int nfull = nbytes >> 4;
     const int nchunks = (nbytes + 15) >> 4;
     const uint4 *d4 = reinterpret_cast<const uint4 *>(w.data);
-    uint64_t nb = 0;  // digital noise: flag masks of up to four rounds
-    int nk = 0, c0 = 0;
     uint32_t flagged = 0;
     if (BITS == 8) {
         const uint4 *rq = reinterpret_cast<const uint4 *>(&sm.ctl->rep);
@@ -666,6 +725,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
             for (; base + 32 <= nfull; base += T) {
                 const int c = base + lane;
                 uint4 v = d4[c];
+                if (PW) pw.x += sq4(v.x, ~0u) + sq4(v.y, ~0u) + sq4(v.z, ~0u) + sq4(v.w, ~0u);
                 uint32_t f0, f1, f2, f3;
                 v.x = rep8_word<MODE>(v.x, k, f0);
                 v.y = rep8_word<MODE>(v.y, k, f1);
@@ -673,9 +733,10 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 v.w = rep8_word<MODE>(v.w, k, f3);
                 const uint32_t bits = chunk_bits(f0, f1, f2, f3);
                 __stcs(o4 + c, v);
+                if (PW) pw.z += sq4(v.x, ~0u) + sq4(v.y, ~0u) + sq4(v.z, ~0u) + sq4(v.w, ~0u);
                 mk[c] = static_cast<uint16_t>(bits);
                 flagged += __popc(bits);
-                if (MODE == 3) noise_collect<8, T>(w, r, p, lane, c, bits, nb, nk, c0);
+                if (MODE == 3) noise_append<8, T, PW>(sm, w, r, p, lane, c, bits, par, pw);
             }
         }
         // warp-uniform rounds: lane handles chunk base + lane
@@ -684,6 +745,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
             uint32_t bits = 0;
             if (c < nchunks) {
                 uint4 v = d4[c];
+                const uint4 vin = v;
                 if (r.active) {
                     uint32_t f0, f1, f2, f3;
                     v.x = rep8_word<MODE>(v.x, k, f0);
@@ -707,17 +769,25 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                     for (int j = 0; j < 16; ++j)
                         if (j < valid) w.out[c * 16 + j] = static_cast<uint8_t>(ww[j >> 2] >> ((j & 3) * 8));
                 }
+                if (PW) {
+                    // the samples of the window only: the ragged chunk's tail bytes are not its own
+                    const int valid = c < nfull ? 16 : nbytes - c * 16;
+                    uint32_t kp[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int nv = valid - 4 * q;
+                        kp[q] = nv >= 4 ? ~0u : (nv <= 0 ? 0u : (1u << (8 * nv)) - 1u);
+                    }
+                    pw.x += sq4(vin.x, kp[0]) + sq4(vin.y, kp[1]) + sq4(vin.z, kp[2]) + sq4(vin.w, kp[3]);
+                    pw.z += sq4(v.x, kp[0]) + sq4(v.y, kp[1]) + sq4(v.z, kp[2]) + sq4(v.w, kp[3]);
+                }
                 flagged += __popc(bits);
                 if (mk) mk[c] = static_cast<uint16_t>(bits);
             }
-            if (MODE == 3) noise_collect<8, T>(w, r, p, lane, c, bits, nb, nk, c0);
+            if (MODE == 3) noise_append<8, T, PW>(sm, w, r, p, lane, c, bits, par, pw);
         }
         if (mk) {
             for (int c = nchunks + tid; c < 2 * w.mask_words; c += T) mk[c] = 0;
-        }
-        if (MODE == 3 && nk) {
-            __syncwarp();
-            if (__any_sync(0xFFFFFFFFu, nb != 0)) noise_batch<8, T>(w, r, p, lane, c0, nb);
         }
     } else {
         uint8_t *mk = reinterpret_cast<uint8_t *>(w.mask);
@@ -735,12 +805,18 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                     const int32_t x = static_cast<int16_t>((ww[j >> 1] >> sh) & 0xFFFFu);
                     const int32_t ad = x > r.M ? x - r.M : r.M - x;
                     const bool fl = r.active && ad >= t && j < valid;
+                    int32_t zo = x;
                     if (fl) {
                         int32_t z = 0;
                         if (MODE == 1) z = p.cval;
                         else if (MODE == 2) z = x > r.M ? r.hiv : r.lov;
                         ww[j >> 1] = (ww[j >> 1] & ~(0xFFFFu << sh)) | ((static_cast<uint32_t>(z) & 0xFFFFu) << sh);
                         bits |= 1u << j;
+                        zo = z;
+                    }
+                    if (PW && j < valid) {
+                        pw.x += static_cast<uint32_t>(x * x);
+                        pw.z += static_cast<uint32_t>(zo * zo);
                     }
                 }
                 flagged += __popc(bits);
@@ -754,14 +830,10 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 }
                 if (mk) mk[c] = static_cast<uint8_t>(bits);
             }
-            if (MODE == 3) noise_collect<12, T>(w, r, p, lane, c, bits, nb, nk, c0);
+            if (MODE == 3) noise_append<12, T, PW>(sm, w, r, p, lane, c, bits, par, pw);
         }
         if (mk) {
             for (int c = nchunks + tid; c < 4 * w.mask_words; c += T) mk[c] = 0;
-        }
-        if (MODE == 3 && nk) {
-            __syncwarp();
-            if (__any_sync(0xFFFFFFFFu, nb != 0)) noise_batch<12, T>(w, r, p, lane, c0, nb);
         }
     }
     return flagged;
@@ -776,32 +848,73 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
 // slot `widx` of the segment and, when release_bar != 0, releases the stage through it.
 // `stage_ok` is this thread's result of waiting for the stage (false: timed out); the first
 // barrier combines it, and the function returns false if any thread of the group timed out.
+//
+// MODE & 3 is the replacement mode (rfi_mode); the other bits select a form of the pass. For
+// the Median-of-MAD variant (Eq. 3), kModeStats runs phases 1-4 only and writes M and D, and
+// kModeApply skips phases 1-4, reads the window's M from sg.med and its dispersion from sg.mad
+// and runs phase 5. kModePower also sums x^2 and z^2 over the window into sg.power.
 template <int BITS, int MODE, int T, int ROWB>
 __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64_t widx, const Params &p,
                                int tid, int par, uint32_t release_bar, bool stage_ok, RowSums &rs) {
     constexpr int NW = T / 32;
+    constexpr bool STATS = (MODE & kModeStats) != 0;
+    constexpr bool APPLY = (MODE & kModeApply) != 0;
+    constexpr bool PW = (MODE & kModePower) != 0;
+    constexpr int RMODE = MODE & 3;
     const int lane = tid & 31;
-    if (stage_ok) phase_histogram<BITS, T, ROWB>(sm, w, tid, par);
-    if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
-    if (BITS == 8) phase_reduce_scan8<T, ROWB>(sm, tid, rs, w.n);
-    else phase_reduce_scan12<T>(sm, tid, w.n);
-    named_bar(sm.bar_id, T);
-    if (tid < 32) phase_search<BITS>(sm, w.n, lane, p.kq, p.cval);
+    if (!APPLY) {
+        if (stage_ok) phase_histogram<BITS, T, ROWB>(sm, w, tid, par);
+        if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
+        if (BITS == 8) phase_reduce_scan8<T, ROWB>(sm, tid, rs, w.n);
+        else phase_reduce_scan12<T>(sm, tid, w.n);
+        named_bar(sm.bar_id, T);
+        if (tid < 32) phase_search<BITS>(sm, w.n, lane, p.kq, p.cval);
+    } else {
+        // every thread has read the previous window's values before this barrier
+        if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
+        if (tid == 0) sm.ctl->rep = make_rep<BITS>(sg.med[widx], sg.mad[widx], p.kq, p.cval);
+    }
     named_bar(sm.bar_id, T);
     const Rep r = load_rep(sm.ctl);
-    uint32_t f = phase_replace<BITS, MODE, T>(sm, w, r, p, tid);
+    uint32_t f = 0;
+    Pow pw = {0u, 0u};
+    if (!STATS) f = phase_replace<BITS, RMODE, T, PW>(sm, w, r, p, tid, par, pw);
+    if (!STATS && RMODE == 3) {
+        named_bar(sm.bar_id, T);  // every flagged position of the window is in the list
+        noise_list<BITS, T, PW>(sm, w, r, p, tid, par, pw);
+    }
     f = __reduce_add_sync(0xFFFFFFFFu, f);
+    unsigned long long px = 0ull, pz = 0ull;
+    if (PW) {  // warp sums in two 16-bit halves, so that no partial sum overflows 32 bits
+        px = (static_cast<unsigned long long>(__reduce_add_sync(0xFFFFFFFFu, pw.x >> 16)) << 16) +
+             __reduce_add_sync(0xFFFFFFFFu, pw.x & 0xFFFFu);
+        pz = (static_cast<unsigned long long>(__reduce_add_sync(0xFFFFFFFFu, pw.z >> 16)) << 16) +
+             __reduce_add_sync(0xFFFFFFFFu, pw.z & 0xFFFFu);
+    }
     if (lane == 0) {
         if (f) atomicAdd(&sm.ctl->count[par], f);
+        if (PW) {
+            atomicAdd(&sm.ctl->pw[par][0], px);
+            atomicAdd(&sm.ctl->pw[par][1], pz);
+        }
         __threadfence_block();
         if (atomicAdd(&sm.ctl->done[par], 1u) == NW - 1) {
             // last warp of this window: every count is in and every read of the stage is done
             __threadfence_block();
             const uint32_t cnt = atomicExch(&sm.ctl->count[par], 0u);
             sm.ctl->done[par] = 0u;
+            if (RMODE == 3) sm.ctl->ncount[par] = 0u;  // every warp has read it
+            if (PW) {
+                const unsigned long long sx = atomicExch(&sm.ctl->pw[par][0], 0ull);
+                const unsigned long long sz = atomicExch(&sm.ctl->pw[par][1], 0ull);
+                if (sg.power) {
+                    sg.power[2 * widx] = sx;
+                    sg.power[2 * widx + 1] = sz;
+                }
+            }
             if (sg.counts) sg.counts[widx] = cnt;
-            if (sg.med) sg.med[widx] = r.M;
-            if (sg.mad) sg.mad[widx] = r.D;
+            if (!APPLY && sg.med) sg.med[widx] = r.M;
+            if (!APPLY && sg.mad) sg.mad[widx] = r.D;
             sm.ctl->flagged += cnt;
             if (BITS == 12 && atomicExch(&sm.ctl->err[par], 0u)) atomicOr(p.status, kStatusSampleRange);
             if (release_bar) mbar_arrive(release_bar);

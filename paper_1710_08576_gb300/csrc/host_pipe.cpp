@@ -87,6 +87,8 @@ using namespace rfi;
 extern "C" rfi_status rfi_excise_host(rfi_plan_t P, const void *const *in, void *const *out,
                                       uint32_t *const *mask, uint32_t *const *counts, void *stream) {
     if (!P) return RFI_ERR_INVALID_ARG;
+    if (P->kmom >= 2) return RFI_ERR_UNSUPPORTED;  // Eq. 3 needs every earlier window's MAD
+    if (P->power) return RFI_ERR_UNSUPPORTED;      // the chunk kernels do not meter power
     rfi_status rs = plan_check_buffers(P, in, out, mask, counts);
     if (rs != RFI_OK) return rs;
     rs = ensure_pipe(P);

@@ -11,6 +11,16 @@ constexpr uint32_t kStatusSampleRange = 1u;  // reported as RFI_ERR_SAMPLE_RANGE
 constexpr uint32_t kStatusTimeout = 2u;      // reported as RFI_ERR_TIMEOUT
 constexpr uint32_t kStatusLayout = 4u;       // unexpected shared-memory window: RFI_ERR_UNSUPPORTED
 
+// Kernel modes beyond the four replacement modes (rfi_mode 0..3), for the Median-of-MAD
+// variant (Eq. 3): a pass that only estimates M and D per window, and passes that apply Eq. 1
+// and Eq. 2 with a per-window centre and dispersion read from memory (kModeApply + rfi_mode).
+constexpr int kModeStats = 4;
+constexpr int kModeApply = 8;
+// Flag bit of the power-metered excision: the kernel also sums x^2 and z^2 over every window
+// (the detected power of the unfiltered and filtered signal, for the improvement metric of
+// Section III-A) and writes them to Seg::power.
+constexpr int kModePower = 16;
+
 // Device counters of one kernel pass, reset before it.
 struct DevCounters {
     unsigned tile_counter;       // dynamic work-list cursor
@@ -32,6 +42,8 @@ struct Seg {
     uint32_t stream_id;   // Philox stream key
     int32_t mask_words;   // ceil(W / 32)
     int32_t vec;          // in/out 16-byte aligned and W * bytes_per_sample % 16 == 0
+    uint64_t *power;      // detected power of window 0: {sum x^2, sum z^2} (nullable)
+    uint32_t pad[2];
 };
 
 // Work-list entry of the persistent kernel: windows [w0, w0 + nw) of segment seg.
@@ -90,6 +102,16 @@ cudaError_t launch_persistent(int bits, int mode, const Shape &s, int grid, cons
 // Plain kernel: one CTA per window of one segment (windows [w_begin, w_begin + nw)).
 cudaError_t launch_stream(int bits, int mode, int consumer_warps, const Seg &seg, int64_t w_begin,
                           int64_t nw, const Params &p, cudaStream_t st);
+
+// Median of MAD (Eq. 3): windows [a, b) of the stream whose window 0 is entry `base` of the
+// per-window MAD and MoM arrays. Mm[base + j] = lower median of D[base + max(0, j-kmom+1) .. j].
+constexpr int kMomChunk = 128;
+struct MomChunk {
+    int64_t base;
+    int32_t a, b;
+};
+cudaError_t launch_mom(int bits, const MomChunk *chunks, int nchunks, const int32_t *D, int32_t *Mm, int kmom,
+                       cudaStream_t st);
 
 // Write n (<= kSegBatch) segment descriptors to dst (device) from kernel parameters.
 constexpr int kSegBatch = 32;

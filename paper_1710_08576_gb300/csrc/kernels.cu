@@ -9,6 +9,14 @@ cudaError_t launch_persistent_b12(int, const Shape &, int, const Seg *, const Ti
                                   unsigned *, int, cudaStream_t);
 int persistent_occupancy_b8(int, const Shape &);
 int persistent_occupancy_b12(int, const Shape &);
+cudaError_t launch_persistent_mom_b8(int, const Shape &, int, const Seg *, const Tile *, int, const Params &,
+                                     unsigned *, int, cudaStream_t);
+cudaError_t launch_persistent_mom_b12(int, const Shape &, int, const Seg *, const Tile *, int, const Params &,
+                                      unsigned *, int, cudaStream_t);
+int persistent_occupancy_mom_b8(int, const Shape &);
+int persistent_occupancy_mom_b12(int, const Shape &);
+cudaError_t launch_mom_b8(const MomChunk *, int, const int32_t *, int32_t *, int, cudaStream_t);
+cudaError_t launch_mom_b12(const MomChunk *, int, const int32_t *, int32_t *, int, cudaStream_t);
 cudaError_t launch_stream_b8(int, int, const Seg &, int64_t, int64_t, const Params &, cudaStream_t);
 cudaError_t launch_stream_b12(int, int, const Seg &, int64_t, int64_t, const Params &, cudaStream_t);
 
@@ -25,13 +33,24 @@ size_t stream_smem_bytes(int bits, int mode, int consumer_warps, int ncopies, in
 }
 
 int persistent_occupancy(int bits, int mode, const Shape &s) {
+    if (mode >= kModeStats)
+        return bits == 8 ? persistent_occupancy_mom_b8(mode, s) : persistent_occupancy_mom_b12(mode, s);
     return bits == 8 ? persistent_occupancy_b8(mode, s) : persistent_occupancy_b12(mode, s);
 }
 
 cudaError_t launch_persistent(int bits, int mode, const Shape &s, int grid, const Seg *segs, const Tile *tiles,
                               int ntiles, const Params &p, unsigned *counter, int inject, cudaStream_t st) {
+    if (mode >= kModeStats)
+        return bits == 8 ? launch_persistent_mom_b8(mode, s, grid, segs, tiles, ntiles, p, counter, inject, st)
+                         : launch_persistent_mom_b12(mode, s, grid, segs, tiles, ntiles, p, counter, inject, st);
     return bits == 8 ? launch_persistent_b8(mode, s, grid, segs, tiles, ntiles, p, counter, inject, st)
                      : launch_persistent_b12(mode, s, grid, segs, tiles, ntiles, p, counter, inject, st);
+}
+
+cudaError_t launch_mom(int bits, const MomChunk *chunks, int nchunks, const int32_t *D, int32_t *Mm, int kmom,
+                       cudaStream_t st) {
+    return bits == 8 ? launch_mom_b8(chunks, nchunks, D, Mm, kmom, st)
+                     : launch_mom_b12(chunks, nchunks, D, Mm, kmom, st);
 }
 
 cudaError_t launch_stream(int bits, int mode, int consumer_warps, const Seg &seg, int64_t w_begin, int64_t nw,

@@ -23,13 +23,15 @@ struct StageMeta {
     int32_t pad[3];
 };
 
-// Dynamic shared memory: the histogram at offset 0 (8-bit: one 64 KiB table for all groups;
-// 12-bit: per group), then one block per consumer group (cumulative counts, control block,
-// mbarriers, stage descriptors), then the stage buffers of every group.
+// Dynamic shared memory: the histogram at offset 0 (8-bit: one table for all groups; 12-bit:
+// per group; none for the apply passes of Eq. 3), then one block per consumer group
+// (cumulative counts, control block, mbarriers, stage descriptors), then the stage buffers of
+// every group.
 struct Layout {
     int grp;        // first group block
     int grp_size;   // bytes per group block
     int cum, ctl, bar, meta;  // offsets inside a group block
+    int nlist;                // digital-noise position list inside a group block (0: none)
     int stage;      // first stage buffer; group g stage s at stage + (g * stages + s) * stage_bytes
     int total;
 };
@@ -37,12 +39,15 @@ struct Layout {
 template <int BITS>
 __host__ __device__ inline Layout layout(int ncopies, int stages, int stage_bytes, int cw, int groups, int mode) {
     Layout L;
-    L.grp = align_up(Geo<BITS>::hist_bytes(ncopies, groups), 128);
+    L.grp = (mode & kModeApply) ? 0 : align_up(Geo<BITS>::hist_bytes(ncopies, groups), 128);
     L.cum = 0;
     L.ctl = align_up(Geo<BITS>::kCumWords * 4, 128);
     L.bar = align_up(L.ctl + static_cast<int>(sizeof(Ctl)), 128);
     L.meta = align_up(L.bar + (2 * kMaxStages + 1) * 8, 128);
-    L.grp_size = align_up(L.meta + kMaxStages * static_cast<int>(sizeof(StageMeta)), 128);
+    const int meta_end = align_up(L.meta + kMaxStages * static_cast<int>(sizeof(StageMeta)), 128);
+    const bool noise = (mode & 3) == 3 && (mode & kModeStats) == 0;
+    L.nlist = noise ? meta_end : 0;
+    L.grp_size = noise ? align_up(meta_end + kNoiseList * 2, 128) : meta_end;
     L.stage = L.grp + groups * L.grp_size;
     L.total = L.stage + groups * stages * stage_bytes;
     return L;
@@ -60,6 +65,7 @@ __device__ __forceinline__ Shm group_view(uint8_t *smem, const Layout &L, int g,
     sm.ctl = reinterpret_cast<Ctl *>(gb + L.ctl);
     sm.ncopies = ncopies;
     sm.bar_id = 1 + g;
+    sm.nlist = L.nlist ? reinterpret_cast<uint16_t *>(gb + L.nlist) : nullptr;
     return sm;
 }
 
@@ -162,11 +168,11 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
             }
             const Tile tl = tiles[t];
             const Seg &sg = segs[tl.seg];
-            // the stage descriptor: lanes 0..3 copy the tile, lanes 4..23 the segment
-            static_assert(sizeof(Tile) == 16 && sizeof(Seg) == 80, "descriptor copy layout");
+            // the stage descriptor: lanes 0..3 copy the tile, lanes 4..27 the segment
+            static_assert(sizeof(Tile) == 16 && sizeof(Seg) == 96, "descriptor copy layout");
             uint32_t *md = reinterpret_cast<uint32_t *>(&meta[s]);
             if (lane < 4) md[lane] = reinterpret_cast<const uint32_t *>(tiles + t)[lane];
-            else if (lane < 24) md[lane] = reinterpret_cast<const uint32_t *>(segs + tl.seg)[lane - 4];
+            else if (lane < 28) md[lane] = reinterpret_cast<const uint32_t *>(segs + tl.seg)[lane - 4];
             uint8_t *stage = stage0 + s * stage_bytes;
             const bool vec = sg.vec != 0;
             const uint8_t *src = sg.in + static_cast<int64_t>(tl.w0) * sg.W * BPS;

@@ -53,18 +53,26 @@ rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req) {
     const int min_stage = static_cast<int>((maxwb + 127) / 128 * 128);
     s.consumer_warps = (req && req->consumer_warps) ? req->consumer_warps : 8;
     s.groups = (req && req->groups) ? req->groups : (s.consumer_warps <= 8 ? 2 : 1);
+    if (P->kmom >= 2 || P->power) {  // these passes are built for one group of 4 or 8 consumer warps
+        if ((req && req->groups > 1) || s.consumer_warps > 8) return RFI_ERR_UNSUPPORTED;
+        s.groups = 1;
+    }
     s.stage_bytes = std::max(min_stage, (req && req->stage_bytes) ? req->stage_bytes : 16384);
     s.stage_bytes = (s.stage_bytes + 127) / 128 * 128;
     s.stages = (req && req->stages) ? req->stages : std::max(2, std::min(4, 65536 / s.stage_bytes));
     s.hist_copies = P->bits == 8 ? 1 : ((req && req->hist_copies) ? req->hist_copies : 2);
     s.dynamic_tiles = (req && req->dynamic_tiles) ? req->dynamic_tiles : (uniform ? 2 : 1);
-    const int want_ctas = (req && req->ctas_per_sm) ? req->ctas_per_sm : (s.groups == 2 ? 1 : 2);
-    if (persistent_smem_bytes(P->bits, P->mode, s) > 227u * 1024u) {
+    const int want_ctas = (req && req->ctas_per_sm) ? req->ctas_per_sm
+                                                    : (P->kmom >= 2 || P->power ? 3 : (s.groups == 2 ? 1 : 2));
+    // the shape is sized for the kernel with the histogram (the MoM stats pass)
+    const int kmode = P->kmom >= 2 ? kModeStats : plan_kernel_mode(P);
+    if (persistent_smem_bytes(P->bits, kmode, s) > 227u * 1024u) {
         if (req && req->stages) return RFI_ERR_UNSUPPORTED;
-        while (s.stages > 1 && persistent_smem_bytes(P->bits, P->mode, s) > 227u * 1024u) --s.stages;
-        if (persistent_smem_bytes(P->bits, P->mode, s) > 227u * 1024u) return RFI_ERR_UNSUPPORTED;
+        while (s.stages > 1 && persistent_smem_bytes(P->bits, kmode, s) > 227u * 1024u) --s.stages;
+        if (persistent_smem_bytes(P->bits, kmode, s) > 227u * 1024u) return RFI_ERR_UNSUPPORTED;
     }
-    const int occ = persistent_occupancy(P->bits, P->mode, s);
+    int occ = persistent_occupancy(P->bits, kmode, s);
+    if (P->kmom >= 2) occ = std::min(occ, persistent_occupancy(P->bits, kModeApply + P->mode, s));
     if (occ < 1) return cudaGetLastError() != cudaSuccess ? RFI_ERR_CUDA : RFI_ERR_UNSUPPORTED;
     s.ctas_per_sm = std::min(want_ctas, occ);
     P->shape = s;
@@ -101,11 +109,21 @@ rfi_status plan_build_tiles(rfi_plan_s *P) {
 
 rfi_status plan_alloc_workspace(rfi_plan_s *P) {
     auto al = [](size_t v) { return (v + 255) / 256 * 256; };
-    const size_t seg_b = al(sizeof(Seg) * P->S);
+    const size_t seg_b = al(sizeof(Seg) * plan_nsegs(P));
     const size_t tile_b = al(sizeof(Tile) * P->tiles_host.size());
     const size_t md_b = al(sizeof(int32_t) * P->total_windows);
     const size_t ctr_b = 256;
-    P->ws_bytes = seg_b + tile_b + 2 * md_b + ctr_b;
+    const bool mom = P->kmom >= 2;
+    if (mom) {
+        P->mchunks.clear();
+        for (int i = 0; i < P->S; ++i)
+            for (int64_t a = 0; a < P->nwin[i]; a += kMomChunk)
+                P->mchunks.push_back(MomChunk{P->woff[i], static_cast<int32_t>(a),
+                                              static_cast<int32_t>(std::min<int64_t>(a + kMomChunk, P->nwin[i]))});
+    }
+    const size_t mc_b = mom ? al(sizeof(MomChunk) * P->mchunks.size()) : 0;
+    const size_t pw_b = P->power ? al(2 * sizeof(uint64_t) * P->total_windows) : 0;
+    P->ws_bytes = seg_b + tile_b + (mom ? 3 : 2) * md_b + mc_b + pw_b + ctr_b;
     if (P->ws) cudaFree(P->ws);
     P->ws = nullptr;
     if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
@@ -122,6 +140,13 @@ rfi_status plan_alloc_workspace(rfi_plan_s *P) {
     RFI_CUDA(cudaMemset(P->ws, 0, P->ws_bytes));
     RFI_CUDA(cudaMemcpy(P->d_tiles, P->tiles_host.data(), sizeof(Tile) * P->tiles_host.size(),
                         cudaMemcpyHostToDevice));
+    if (mom) {
+        P->d_mom = reinterpret_cast<int32_t *>(b + ctr_b + seg_b + tile_b + 2 * md_b);
+        P->d_mchunks = reinterpret_cast<MomChunk *>(b + ctr_b + seg_b + tile_b + 3 * md_b);
+        RFI_CUDA(cudaMemcpy(P->d_mchunks, P->mchunks.data(), sizeof(MomChunk) * P->mchunks.size(),
+                            cudaMemcpyHostToDevice));
+    }
+    if (P->power) P->d_pow = reinterpret_cast<uint64_t *>(b + ctr_b + seg_b + tile_b + 2 * md_b + mc_b);
     P->segs_valid = false;
     return RFI_OK;
 }
@@ -141,9 +166,22 @@ Params plan_params(const rfi_plan_s *P) {
 // Enqueue the persistent launch (with its counter reset) on st.
 rfi_status plan_enqueue_batched(rfi_plan_s *P, cudaStream_t st) {
     RFI_CUDA(cudaMemsetAsync(P->d_ctr, 0, sizeof(DevCounters), st));
-    RFI_CUDA(launch_persistent(P->bits, P->mode, P->shape, P->grid, P->d_segs, P->d_tiles, P->ntiles,
-                               plan_params(P), &P->d_ctr->tile_counter,
-                               (P->flags & RFI_PLAN_INJECT_TIMEOUT) ? 1 : 0, st));
+    const int inject = (P->flags & RFI_PLAN_INJECT_TIMEOUT) ? 1 : 0;
+    if (P->kmom < 2) {
+        RFI_CUDA(launch_persistent(P->bits, plan_kernel_mode(P), P->shape, P->grid, P->d_segs, P->d_tiles,
+                                   P->ntiles, plan_params(P), &P->d_ctr->tile_counter, inject, st));
+        return RFI_OK;
+    }
+    // Median of MAD (Eq. 3): M and D of every window, the sliding median of the MADs, then Eq. 1
+    // and Eq. 2 with each window's M and its MoM (segment entries S..2S-1)
+    const Params p = plan_params(P);
+    RFI_CUDA(launch_persistent(P->bits, kModeStats, P->shape, P->grid, P->d_segs, P->d_tiles, P->ntiles, p,
+                               &P->d_ctr->tile_counter, inject, st));
+    RFI_CUDA(launch_mom(P->bits, P->d_mchunks, static_cast<int>(P->mchunks.size()), P->d_mad, P->d_mom, P->kmom,
+                        st));
+    RFI_CUDA(cudaMemsetAsync(&P->d_ctr->tile_counter, 0, sizeof(unsigned), st));
+    RFI_CUDA(launch_persistent(P->bits, kModeApply + P->mode, P->shape, P->grid, P->d_segs + P->S, P->d_tiles,
+                               P->ntiles, p, &P->d_ctr->tile_counter, 0, st));
     return RFI_OK;
 }
 
@@ -173,7 +211,7 @@ rfi_status plan_build_graph(rfi_plan_s *P) {
 std::vector<Seg> plan_segs(const rfi_plan_s *P, const void *const *in, void *const *out, uint32_t *const *mask,
                            uint32_t *const *counts) {
     const int bps = P->bits == 8 ? 1 : 2;
-    std::vector<Seg> segs(P->S);
+    std::vector<Seg> segs(plan_nsegs(P));
     for (int i = 0; i < P->S; ++i) {
         Seg &g = segs[i];
         std::memset(&g, 0, sizeof(Seg));
@@ -183,6 +221,7 @@ std::vector<Seg> plan_segs(const rfi_plan_s *P, const void *const *in, void *con
         g.counts = counts ? counts[i] : nullptr;
         g.med = P->d_med + P->woff[i];
         g.mad = P->d_mad + P->woff[i];
+        g.power = P->power ? P->d_pow + 2 * P->woff[i] : nullptr;
         g.len = P->len[i];
         g.abs0 = 0;
         g.W = P->W[i];
@@ -190,6 +229,15 @@ std::vector<Seg> plan_segs(const rfi_plan_s *P, const void *const *in, void *con
         g.mask_words = (P->W[i] + 31) / 32;
         g.vec = ((reinterpret_cast<uintptr_t>(in[i]) | reinterpret_cast<uintptr_t>(out[i])) % 16 == 0) &&
                 (static_cast<int64_t>(P->W[i]) * bps) % 16 == 0;
+        if (P->kmom >= 2) {
+            // apply pass: reads M and the MoM, writes the outputs; stats pass: writes M and D only
+            Seg &a = segs[P->S + i];
+            a = g;
+            a.mad = P->d_mom + P->woff[i];
+            g.out = const_cast<uint8_t *>(g.in);
+            g.mask = nullptr;
+            g.counts = nullptr;
+        }
     }
     return segs;
 }
@@ -238,11 +286,15 @@ rfi_status rfi_plan_create(const rfi_plan_desc *d, rfi_plan_t *out_plan) {
     if (!(d->k > 0.0) || !std::isfinite(d->k) || d->k > 1.0e6) return RFI_ERR_INVALID_ARG;
     if (d->mode < RFI_REPLACE_ZERO || d->mode > RFI_REPLACE_NOISE) return RFI_ERR_INVALID_ARG;
     const uint32_t known = RFI_PLAN_PER_STREAM | RFI_PLAN_BATCHED | RFI_PLAN_GRAPH | RFI_PLAN_AUTOTUNE |
-                           RFI_PLAN_INJECT_TIMEOUT;
+                           RFI_PLAN_INJECT_TIMEOUT | RFI_PLAN_POWER;
     if (d->flags & ~known) return RFI_ERR_INVALID_ARG;
     if ((d->flags & RFI_PLAN_PER_STREAM) && (d->flags & (RFI_PLAN_BATCHED | RFI_PLAN_GRAPH)))
         return RFI_ERR_INVALID_ARG;
     if (d->shape && !valid_shape(*d->shape)) return RFI_ERR_INVALID_ARG;
+    if (d->mom_windows < 0 || d->mom_windows > (1 << 20)) return RFI_ERR_INVALID_ARG;
+    if (d->mom_windows >= 2 && (d->flags & RFI_PLAN_PER_STREAM)) return RFI_ERR_UNSUPPORTED;
+    if ((d->flags & RFI_PLAN_POWER) && ((d->flags & RFI_PLAN_PER_STREAM) || d->mom_windows >= 2))
+        return RFI_ERR_UNSUPPORTED;
     // Kq = round_half_up(k * 1.4826 * 2^16) (fixed-point multiple of Eq. 1)
     const int64_t kq = static_cast<int64_t>(std::floor(d->k * 1.4826 * 65536.0 + 0.5));
     if (kq < 1) return RFI_ERR_INVALID_ARG;
@@ -267,6 +319,8 @@ rfi_status rfi_plan_create(const rfi_plan_desc *d, rfi_plan_t *out_plan) {
     const int32_t lo = P->bits == 8 ? -128 : -2048, hi = P->bits == 8 ? 127 : 2047;
     P->cval = std::min(hi, std::max(lo, d->const_value));
     P->seed = d->seed;
+    P->kmom = d->mom_windows >= 2 ? d->mom_windows : 0;
+    P->power = (d->flags & RFI_PLAN_POWER) != 0;
     P->len.assign(d->stream_len, d->stream_len + P->S);
     P->W.assign(d->window_len, d->window_len + P->S);
     P->sid.resize(P->S);
@@ -292,7 +346,8 @@ rfi_status rfi_plan_create(const rfi_plan_desc *d, rfi_plan_t *out_plan) {
     rs = plan_choose_shape(P, d->shape);
     if (rs == RFI_OK) rs = plan_build_tiles(P);
     if (rs == RFI_OK) rs = plan_alloc_workspace(P);
-    if (rs == RFI_OK && (P->flags & RFI_PLAN_AUTOTUNE) && !(P->flags & RFI_PLAN_PER_STREAM))
+    if (rs == RFI_OK && (P->flags & RFI_PLAN_AUTOTUNE) && !(P->flags & RFI_PLAN_PER_STREAM) && P->kmom < 2 &&
+        !P->power)
         rs = plan_autotune(P, d->shape);
     if (rs == RFI_OK && (P->flags & RFI_PLAN_GRAPH)) rs = plan_build_graph(P);
     if (rs != RFI_OK) {
@@ -318,12 +373,13 @@ rfi_status rfi_excise(rfi_plan_t P, const void *const *in, void *const *out, uin
             RFI_CUDA(launch_stream(P->bits, P->mode, P->shape.consumer_warps, segs[i], 0, P->nwin[i], p, st));
         return RFI_OK;
     }
-    if (!P->segs_valid || std::memcmp(segs.data(), P->segs_host.data(), sizeof(Seg) * P->S) != 0) {
-        for (int i = 0; i < P->S; i += kSegBatch)
-            RFI_CUDA(launch_write_segs(P->d_segs + i, segs.data() + i, std::min(kSegBatch, P->S - i), st));
+    const int nsegs = plan_nsegs(P);
+    if (!P->segs_valid || std::memcmp(segs.data(), P->segs_host.data(), sizeof(Seg) * nsegs) != 0) {
+        for (int i = 0; i < nsegs; i += kSegBatch)
+            RFI_CUDA(launch_write_segs(P->d_segs + i, segs.data() + i, std::min(kSegBatch, nsegs - i), st));
         P->segs_host = segs;
         P->segs_valid = true;
-        P->last_seg_writes = (P->S + kSegBatch - 1) / kSegBatch;
+        P->last_seg_writes = (nsegs + kSegBatch - 1) / kSegBatch;
     } else {
         P->last_seg_writes = 0;
     }
@@ -359,6 +415,65 @@ rfi_status rfi_stats(rfi_plan_t P, int32_t *const *median, int32_t *const *mad, 
     return dev;
 }
 
+rfi_status rfi_stats_mom(rfi_plan_t P, int32_t *const *mom, void *stream) {
+    if (!P) return RFI_ERR_INVALID_ARG;
+    if (P->kmom < 2) return RFI_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int i = 0; i < P->S; ++i)
+        if (mom && mom[i])
+            RFI_CUDA(cudaMemcpyAsync(mom[i], P->d_mom + P->woff[i], sizeof(int32_t) * P->nwin[i],
+                                     cudaMemcpyDeviceToDevice, st));
+    return RFI_OK;
+}
+
+rfi_status rfi_stats_power(rfi_plan_t P, uint64_t *const *power, void *stream) {
+    if (!P) return RFI_ERR_INVALID_ARG;
+    if (!P->power) return RFI_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int i = 0; i < P->S; ++i)
+        if (power && power[i])
+            RFI_CUDA(cudaMemcpyAsync(power[i], P->d_pow + 2 * P->woff[i], 2 * sizeof(uint64_t) * P->nwin[i],
+                                     cudaMemcpyDeviceToDevice, st));
+    return RFI_OK;
+}
+
+rfi_status rfi_improvement_db(const uint64_t *power, int64_t nwin, int32_t windows_per_point,
+                              int32_t points_per_block, double *db, double *s_unfiltered, double *s_filtered) {
+    if (!power || nwin < 1 || windows_per_point < 1 || points_per_block < 2 || !db) return RFI_ERR_INVALID_ARG;
+    const int64_t npt = nwin / windows_per_point;
+    const int64_t nb = npt / points_per_block;
+    double s[2] = {0.0, 0.0};
+    for (int side = 0; side < 2; ++side) {
+        double acc = 0.0;
+        int64_t used = 0;
+        std::vector<double> pt(points_per_block);
+        for (int64_t b = 0; b < nb; ++b) {
+            double mean = 0.0;
+            for (int32_t q = 0; q < points_per_block; ++q) {
+                double v = 0.0;
+                const int64_t w0 = (b * points_per_block + q) * windows_per_point;
+                for (int32_t k = 0; k < windows_per_point; ++k) v += static_cast<double>(power[2 * (w0 + k) + side]);
+                pt[q] = v;
+                mean += v;
+            }
+            mean /= points_per_block;
+            double var = 0.0;
+            for (double v : pt) var += (v - mean) * (v - mean);
+            const double rms = std::sqrt(var / points_per_block);
+            if (rms > 0.0) {
+                acc += mean / rms;
+                ++used;
+            }
+        }
+        if (used == 0) return RFI_ERR_INVALID_ARG;
+        s[side] = acc / static_cast<double>(used);
+    }
+    *db = 10.0 * std::log10(s[1] / s[0]);
+    if (s_unfiltered) *s_unfiltered = s[0];
+    if (s_filtered) *s_filtered = s[1];
+    return RFI_OK;
+}
+
 rfi_status rfi_plan_get_info(rfi_plan_t P, rfi_plan_info *info) {
     if (!P || !info) return RFI_ERR_INVALID_ARG;
     std::memset(info, 0, sizeof(*info));
@@ -376,7 +491,7 @@ rfi_status rfi_plan_get_info(rfi_plan_t P, rfi_plan_info *info) {
     info->shape.hist_copies = P->shape.hist_copies;
     info->shape.groups = P->shape.groups;
     info->sm_count = P->sm_count;
-    info->kernels_per_call = (P->flags & RFI_PLAN_PER_STREAM) ? P->S : 1;
+    info->kernels_per_call = (P->flags & RFI_PLAN_PER_STREAM) ? P->S : (P->kmom >= 2 ? 3 : 1);
     return RFI_OK;
 }
 

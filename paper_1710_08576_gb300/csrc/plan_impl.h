@@ -49,6 +49,14 @@ struct rfi_plan_s {
     rfi::Seg *d_segs = nullptr;
     rfi::Tile *d_tiles = nullptr;
     int32_t *d_med = nullptr, *d_mad = nullptr;
+    // Median of MAD (Eq. 3): kmom >= 2; segment table holds 2S entries (stats pass, apply pass)
+    int kmom = 0;
+    int32_t *d_mom = nullptr;
+    // RFI_PLAN_POWER: {sum x^2, sum z^2} per window
+    bool power = false;
+    uint64_t *d_pow = nullptr;
+    rfi::MomChunk *d_mchunks = nullptr;
+    std::vector<rfi::MomChunk> mchunks;
     std::vector<rfi::Seg> segs_host;
     bool segs_valid = false;
     int last_seg_writes = 0;
@@ -72,5 +80,8 @@ std::vector<Seg> plan_segs(const rfi_plan_s *P, const void *const *in, void *con
                            uint32_t *const *counts);
 rfi_status plan_check_buffers(const rfi_plan_s *P, const void *const *in, void *const *out,
                               uint32_t *const *mask, uint32_t *const *counts);
+inline int plan_nsegs(const rfi_plan_s *P) { return P->kmom >= 2 ? 2 * P->S : P->S; }
+// Kernel mode of a per-window MAD plan (the power-metered form when RFI_PLAN_POWER is set).
+inline int plan_kernel_mode(const rfi_plan_s *P) { return P->mode | (P->power ? kModePower : 0); }
 
 }  // namespace rfi

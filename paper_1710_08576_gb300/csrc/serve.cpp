@@ -112,12 +112,12 @@ struct Request {
     float lat_ms = 0.f;      // submit -> last pass (device requests)
 };
 
+// Per-pass upload: the segment table followed by the work list, staged in pinned memory and
+// copied to the device in one transfer.
 struct Slot {
-    Seg *d_segs = nullptr;
-    Tile *d_tiles = nullptr;
-    DevCounters *d_ctr = nullptr;
-    Tile *h_tiles = nullptr;       // pinned
-    DevCounters *h_ctr = nullptr;  // pinned
+    uint8_t *d_buf = nullptr;  // device: segs at 0, tiles at tiles_off
+    uint8_t *h_buf = nullptr;  // pinned host staging of the same layout
+    size_t tiles_off = 0;
     int max_segs = 0;
 };
 
@@ -157,6 +157,7 @@ struct rfi_server_s {
     std::vector<rfi::Pass> inflight;
     rfi::Slot slots[rfi::kSlots];
     bool slot_busy[rfi::kSlots] = {false, false};
+    rfi::DevCounters *d_ctr = nullptr;  // status and flagged total of every pass (never reset)
     cudaStream_t s_copy = nullptr, s_comp = nullptr, s_back = nullptr;
     cudaEvent_t ev_copies = nullptr;
     uint64_t next_ticket = 1;
@@ -180,7 +181,7 @@ namespace {
         if ((x) != cudaSuccess) return RFI_ERR_CUDA;         \
     } while (0)
 
-Params server_params(const rfi_server_s *s, DevCounters *ctr) {
+Params server_params(const rfi_server_s *s, DevCounters *ctr) {  // ctr: the server's counters
     Params p;
     p.kq = s->kq;
     p.seed = s->seed;
@@ -203,9 +204,6 @@ rfi_status poll_all(rfi_server_s *s) {
         const cudaError_t q = cudaEventQuery(ps.ev);
         if (q == cudaErrorNotReady) break;
         if (q != cudaSuccess) return RFI_ERR_CUDA;
-        const DevCounters &c = *s->slots[ps.slot].h_ctr;
-        s->flagged += c.flagged;
-        s->status |= c.status;
         for (auto &cp : ps.completes) {
             Ring &r = s->rings[cp.first];
             s->samples_done += static_cast<uint64_t>(cp.second - r.completed);
@@ -341,8 +339,9 @@ rfi_status rfi_server_create(const rfi_server_desc *d, rfi_server_t *out) {
         ring_bytes += 2 * al256(r.cap * s->bps) + al256(r.nslots * r.mw * 4) + 3 * al256(r.nslots * 4);
     }
     const int max_segs = 2 * s->S + s->max_requests;
-    const size_t slot_bytes = al256(sizeof(Seg) * max_segs) + al256(sizeof(Tile) * kMaxPassTiles) + 256;
-    const size_t need = ring_bytes + kSlots * slot_bytes;
+    const size_t tiles_off = al256(sizeof(Seg) * max_segs);
+    const size_t slot_bytes = tiles_off + al256(sizeof(Tile) * kMaxPassTiles);
+    const size_t need = ring_bytes + kSlots * slot_bytes + 256;
     if (d->memory_budget < need) {
         delete s;
         return RFI_ERR_OOM;
@@ -368,14 +367,13 @@ rfi_status rfi_server_create(const rfi_server_desc *d, rfi_server_t *out) {
         r.mad = reinterpret_cast<int32_t *>(take(r.nslots * 4));
     }
     bool ok = true;
+    s->d_ctr = reinterpret_cast<DevCounters *>(take(256));
     for (int k = 0; k < kSlots && ok; ++k) {
         Slot &sl = s->slots[k];
         sl.max_segs = max_segs;
-        sl.d_segs = reinterpret_cast<Seg *>(take(sizeof(Seg) * max_segs));
-        sl.d_tiles = reinterpret_cast<Tile *>(take(sizeof(Tile) * kMaxPassTiles));
-        sl.d_ctr = reinterpret_cast<DevCounters *>(take(256));
-        ok = cudaMallocHost(&sl.h_tiles, sizeof(Tile) * kMaxPassTiles) == cudaSuccess &&
-             cudaMallocHost(&sl.h_ctr, sizeof(DevCounters)) == cudaSuccess;
+        sl.tiles_off = tiles_off;
+        sl.d_buf = take(slot_bytes);
+        ok = cudaMallocHost(&sl.h_buf, slot_bytes) == cudaSuccess;
     }
     ok = ok && cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking) == cudaSuccess &&
          cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking) == cudaSuccess &&
@@ -563,7 +561,7 @@ rfi_status rfi_server_step(rfi_server_t s, int32_t *launched) {
     sh.consumer_warps = 8;
     sh.groups = 1;
     sh.hist_copies = s->bits == 8 ? 1 : 2;
-    sh.dynamic_tiles = 1;
+    sh.dynamic_tiles = 2;  // static round robin: no work-list cursor to reset between passes
     sh.stage_bytes = (max_wb + 127) / 128 * 128;
     sh.stages = 2;
     while (sh.stages > 1 && persistent_smem_bytes(s->bits, s->mode, sh) > 227u * 1024u) --sh.stages;
@@ -575,22 +573,22 @@ rfi_status rfi_server_step(rfi_server_t s, int32_t *launched) {
         add_tiles(tiles, static_cast<uint32_t>(i), segs[i].len, segs[i].W, s->bps, sh.stage_bytes);
     if (static_cast<int>(tiles.size()) > kMaxPassTiles || static_cast<int>(segs.size()) > sl.max_segs)
         return RFI_ERR_UNSUPPORTED;
-    std::memcpy(sl.h_tiles, tiles.data(), sizeof(Tile) * tiles.size());
+    // one pinned upload: segment table, then the work list (the slot is free, so its staging
+    // buffer is no longer read by an earlier copy)
+    std::memcpy(sl.h_buf, segs.data(), sizeof(Seg) * segs.size());
+    std::memcpy(sl.h_buf + sl.tiles_off, tiles.data(), sizeof(Tile) * tiles.size());
     // the pass sees every copy enqueued so far
     SRV_CUDA(cudaEventRecord(s->ev_copies, s->s_copy));
     SRV_CUDA(cudaStreamWaitEvent(s->s_comp, s->ev_copies, 0));
     SRV_CUDA(cudaEventCreate(&ps.ev0));
     SRV_CUDA(cudaEventRecord(ps.ev0, s->s_comp));
-    for (size_t i = 0; i < segs.size(); i += kSegBatch)
-        SRV_CUDA(launch_write_segs(sl.d_segs + i, segs.data() + i,
-                                   static_cast<int>(std::min<size_t>(kSegBatch, segs.size() - i)), s->s_comp));
-    SRV_CUDA(cudaMemcpyAsync(sl.d_tiles, sl.h_tiles, sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s->s_comp));
-    SRV_CUDA(cudaMemsetAsync(sl.d_ctr, 0, sizeof(DevCounters), s->s_comp));
+    const size_t up = sl.tiles_off + sizeof(Tile) * tiles.size();
+    SRV_CUDA(cudaMemcpyAsync(sl.d_buf, sl.h_buf, up, cudaMemcpyHostToDevice, s->s_comp));
     const int ntiles = static_cast<int>(tiles.size());
     const int grid = std::max(1, std::min(ntiles, s->sm_count * sh.ctas_per_sm));
-    SRV_CUDA(launch_persistent(s->bits, s->mode, sh, grid, sl.d_segs, sl.d_tiles, ntiles, server_params(s, sl.d_ctr),
-                               &sl.d_ctr->tile_counter, 0, s->s_comp));
-    SRV_CUDA(cudaMemcpyAsync(sl.h_ctr, sl.d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s->s_comp));
+    SRV_CUDA(launch_persistent(s->bits, s->mode, sh, grid, reinterpret_cast<const Seg *>(sl.d_buf),
+                               reinterpret_cast<const Tile *>(sl.d_buf + sl.tiles_off), ntiles,
+                               server_params(s, s->d_ctr), nullptr, 0, s->s_comp));
     SRV_CUDA(cudaEventCreate(&ps.ev));
     SRV_CUDA(cudaEventRecord(ps.ev, s->s_comp));
     // host requests finishing here: copy results back after the pass
@@ -607,11 +605,14 @@ rfi_status rfi_server_step(rfi_server_t s, int32_t *launched) {
             SRV_CUDA(cudaEventRecord(rq.ev_done, s->s_back));
         }
     }
-    // chunks whose last sample is now scheduled complete with this pass
+    // a chunk is done with the pass that excises the last window ending inside it (its trailing
+    // partial window belongs to the chunk that completes it, or to the flush)
     for (size_t k = 0; k < s->chunks.size(); ++k) {
         Chunk &ch = s->chunks[k];
         if (ch.assigned) continue;
-        if (ch.end <= s->rings[ch.stream].sched) {
+        const Ring &r = s->rings[ch.stream];
+        const int64_t need = r.flushing ? ch.end : r.start + (ch.end - r.start) / r.W * r.W;
+        if (need <= r.sched) {
             ch.assigned = true;
             ps.chunks.push_back(k + s->chunk_base);
         }
@@ -757,6 +758,11 @@ rfi_status rfi_server_get_stats(rfi_server_t s, rfi_server_stats *st) {
     if (!s || !st) return RFI_ERR_INVALID_ARG;
     rfi_status rs = poll_all(s);
     if (rs != RFI_OK) return rs;
+    DevCounters c;  // totals of the passes that finished (and of any still running)
+    SRV_CUDA(cudaMemcpyAsync(&c, s->d_ctr, sizeof(c), cudaMemcpyDeviceToHost, s->s_back));
+    SRV_CUDA(cudaStreamSynchronize(s->s_back));
+    s->flagged = c.flagged;
+    s->status = c.status;
     std::memset(st, 0, sizeof(*st));
     const std::vector<double> &cl = s->chunk_lat, &rl = s->req_lat;
     st->passes = static_cast<uint64_t>(s->passes_done);
@@ -796,10 +802,8 @@ rfi_status rfi_server_destroy(rfi_server_t s) {
         if (rq.ev_submit) cudaEventDestroy(rq.ev_submit);
         if (rq.ev_done) cudaEventDestroy(rq.ev_done);
     }
-    for (auto &sl : s->slots) {
-        if (sl.h_tiles) cudaFreeHost(sl.h_tiles);
-        if (sl.h_ctr) cudaFreeHost(sl.h_ctr);
-    }
+    for (auto &sl : s->slots)
+        if (sl.h_buf) cudaFreeHost(sl.h_buf);
     if (s->ev_copies) cudaEventDestroy(s->ev_copies);
     if (s->s_copy) cudaStreamDestroy(s->s_copy);
     if (s->s_comp) cudaStreamDestroy(s->s_comp);

@@ -127,3 +127,14 @@ def test_server_invalid_arguments_fail_before_cuda():
     d = rfi.RfiServerDesc(8, n, w, None, starts, 1 << 16, 3.0, 0, 0, 0, 1 << 30, 1, 0)
     assert rfi.rfi_server_create(d)[0] == rfi.RFI_ERR_INVALID_ARG
     assert rfi.LIB.rfi_server_destroy(None) == rfi.RFI_OK
+
+
+def test_mom_arguments_checked_before_cuda():
+    lens = (ctypes.c_int64 * 1)(4096)
+    wins = (ctypes.c_int32 * 1)(1024)
+    h = ctypes.c_void_p()
+    for kmom, flags, want in ((-1, 0, rfi.RFI_ERR_INVALID_ARG), ((1 << 20) + 1, 0, rfi.RFI_ERR_INVALID_ARG),
+                              (4, rfi.RFI_PLAN_PER_STREAM, rfi.RFI_ERR_UNSUPPORTED)):
+        d = rfi.RfiPlanDesc(8, 1, lens, wins, None, 3.0, 0, 0, 0, flags, None, kmom)
+        assert rfi.LIB.rfi_plan_create(ctypes.byref(d), ctypes.byref(h)) == want
+    assert rfi.LIB.rfi_stats_mom(None, None, None) == rfi.RFI_ERR_INVALID_ARG
