@@ -146,8 +146,11 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t *rk0, const uint32_t *rk1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        // one 32 x 32 -> 64-bit product per multiplier gives both halves
+        const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
+        const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
+        const uint32_t lo0 = static_cast<uint32_t>(p0), hi0 = static_cast<uint32_t>(p0 >> 32);
+        const uint32_t lo1 = static_cast<uint32_t>(p1), hi1 = static_cast<uint32_t>(p1 >> 32);
         c = make_uint4(hi1 ^ c.y ^ rk0[r], lo1, hi0 ^ c.w ^ rk1[r], lo0);
     }
     return c;
@@ -852,10 +855,12 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
 // MODE & 3 is the replacement mode (rfi_mode); the other bits select a form of the pass. For
 // the Median-of-MAD variant (Eq. 3), kModeStats runs phases 1-4 only and writes M and D, and
 // kModeApply skips phases 1-4, reads the window's M from sg.med and its dispersion from sg.mad
-// and runs phase 5. kModePower also sums x^2 and z^2 over the window into sg.power.
+// and runs phase 5 (amd, when given, holds the window's {M, dispersion} in shared memory).
+// kModePower also sums x^2 and z^2 over the window into sg.power.
 template <int BITS, int MODE, int T, int ROWB>
 __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64_t widx, const Params &p,
-                               int tid, int par, uint32_t release_bar, bool stage_ok, RowSums &rs) {
+                               int tid, int par, uint32_t release_bar, bool stage_ok, RowSums &rs,
+                               const int2 *amd = nullptr) {
     constexpr int NW = T / 32;
     constexpr bool STATS = (MODE & kModeStats) != 0;
     constexpr bool APPLY = (MODE & kModeApply) != 0;
@@ -872,7 +877,10 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
     } else {
         // every thread has read the previous window's values before this barrier
         if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
-        if (tid == 0) sm.ctl->rep = make_rep<BITS>(sg.med[widx], sg.mad[widx], p.kq, p.cval);
+        if (tid == 0) {  // from the stage's copy (amd) when the copy warp brought it along
+            const int2 md = amd ? *amd : make_int2(sg.med[widx], sg.mad[widx]);
+            sm.ctl->rep = make_rep<BITS>(md.x, md.y, p.kq, p.cval);
+        }
     }
     named_bar(sm.bar_id, T);
     const Rep r = load_rep(sm.ctl);

@@ -16,6 +16,7 @@ constexpr uint32_t kStatusLayout = 4u;       // unexpected shared-memory window:
 // and Eq. 2 with a per-window centre and dispersion read from memory (kModeApply + rfi_mode).
 constexpr int kModeStats = 4;
 constexpr int kModeApply = 8;
+constexpr int kApplyTileWindows = 32;  // at most this many windows per tile in apply passes
 // Flag bit of the power-metered excision: the kernel also sums x^2 and z^2 over every window
 // (the detected power of the unfiltered and filtered signal, for the improvement metric of
 // Section III-A) and writes them to Seg::power.

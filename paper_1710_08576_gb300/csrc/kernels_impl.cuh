@@ -32,6 +32,7 @@ struct Layout {
     int grp_size;   // bytes per group block
     int cum, ctl, bar, meta;  // offsets inside a group block
     int nlist;                // digital-noise position list inside a group block (0: none)
+    int amd;                  // apply passes: per stage, {M, dispersion} of its windows (0: none)
     int stage;      // first stage buffer; group g stage s at stage + (g * stages + s) * stage_bytes
     int total;
 };
@@ -47,7 +48,10 @@ __host__ __device__ inline Layout layout(int ncopies, int stages, int stage_byte
     const int meta_end = align_up(L.meta + kMaxStages * static_cast<int>(sizeof(StageMeta)), 128);
     const bool noise = (mode & 3) == 3 && (mode & kModeStats) == 0;
     L.nlist = noise ? meta_end : 0;
-    L.grp_size = noise ? align_up(meta_end + kNoiseList * 2, 128) : meta_end;
+    const int list_end = noise ? align_up(meta_end + kNoiseList * 2, 128) : meta_end;
+    const bool apply = (mode & kModeApply) != 0;
+    L.amd = apply ? list_end : 0;
+    L.grp_size = apply ? align_up(list_end + kMaxStages * kApplyTileWindows * 8, 128) : list_end;
     L.stage = L.grp + groups * L.grp_size;
     L.total = L.stage + groups * stages * stage_bytes;
     return L;
@@ -175,6 +179,11 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
             else if (lane < 28) md[lane] = reinterpret_cast<const uint32_t *>(segs + tl.seg)[lane - 4];
             uint8_t *stage = stage0 + s * stage_bytes;
             const bool vec = sg.vec != 0;
+            if ((MODE & kModeApply) && static_cast<uint32_t>(lane) < tl.nw && tl.nw <= kApplyTileWindows) {
+                // the centre and dispersion of the tile's windows ride along with the stage
+                int2 *amd = reinterpret_cast<int2 *>(gb + L.amd) + s * kApplyTileWindows;
+                amd[lane] = make_int2(sg.med[tl.w0 + lane], sg.mad[tl.w0 + lane]);
+            }
             const uint8_t *src = sg.in + static_cast<int64_t>(tl.w0) * sg.W * BPS;
             const uint32_t bulk = vec ? (tl.bytes & ~15u) : 0u, rem = tl.bytes & 15u;
             if (vec && static_cast<uint32_t>(lane) < rem) stage[bulk + lane] = src[bulk + lane];
@@ -227,8 +236,11 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
         for (uint32_t k = 0; k < tl.nw && alive; ++k) {
             const int64_t widx = static_cast<int64_t>(tl.w0) + k;
             const Win win = make_win(sg, widx, stage + k * sg.W * BPS, BPS);
+            const int2 *amd = ((MODE & kModeApply) && tl.nw <= kApplyTileWindows)
+                                  ? reinterpret_cast<const int2 *>(gb + L.amd) + s * kApplyTileWindows + k
+                                  : nullptr;
             alive = process_window<BITS, MODE, T, Geo<BITS>::row_bytes(G)>(
-                sm, win, sg, widx, p, tid, par, k + 1 == tl.nw ? empty_bar(s) : 0u, true, rs);
+                sm, win, sg, widx, p, tid, par, k + 1 == tl.nw ? empty_bar(s) : 0u, true, rs, amd);
             par ^= 1;
         }
         if (!alive) {

@@ -52,18 +52,17 @@ rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req) {
     }
     const int min_stage = static_cast<int>((maxwb + 127) / 128 * 128);
     s.consumer_warps = (req && req->consumer_warps) ? req->consumer_warps : 8;
-    s.groups = (req && req->groups) ? req->groups : (s.consumer_warps <= 8 ? 2 : 1);
+    s.groups = (req && req->groups) ? req->groups : 1;
     if (P->kmom >= 2 || P->power) {  // these passes are built for one group of 4 or 8 consumer warps
         if ((req && req->groups > 1) || s.consumer_warps > 8) return RFI_ERR_UNSUPPORTED;
         s.groups = 1;
     }
     s.stage_bytes = std::max(min_stage, (req && req->stage_bytes) ? req->stage_bytes : 16384);
     s.stage_bytes = (s.stage_bytes + 127) / 128 * 128;
-    s.stages = (req && req->stages) ? req->stages : std::max(2, std::min(4, 65536 / s.stage_bytes));
+    s.stages = (req && req->stages) ? req->stages : 2;
     s.hist_copies = P->bits == 8 ? 1 : ((req && req->hist_copies) ? req->hist_copies : 2);
     s.dynamic_tiles = (req && req->dynamic_tiles) ? req->dynamic_tiles : (uniform ? 2 : 1);
-    const int want_ctas = (req && req->ctas_per_sm) ? req->ctas_per_sm
-                                                    : (P->kmom >= 2 || P->power ? 3 : (s.groups == 2 ? 1 : 2));
+    const int want_ctas = (req && req->ctas_per_sm) ? req->ctas_per_sm : 4;  // as many as fit, up to 4
     // the shape is sized for the kernel with the histogram (the MoM stats pass)
     const int kmode = P->kmom >= 2 ? kModeStats : plan_kernel_mode(P);
     if (persistent_smem_bytes(P->bits, kmode, s) > 227u * 1024u) {
@@ -71,10 +70,15 @@ rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req) {
         while (s.stages > 1 && persistent_smem_bytes(P->bits, kmode, s) > 227u * 1024u) --s.stages;
         if (persistent_smem_bytes(P->bits, kmode, s) > 227u * 1024u) return RFI_ERR_UNSUPPORTED;
     }
-    int occ = persistent_occupancy(P->bits, kmode, s);
-    if (P->kmom >= 2) occ = std::min(occ, persistent_occupancy(P->bits, kModeApply + P->mode, s));
+    const int occ = persistent_occupancy(P->bits, kmode, s);
     if (occ < 1) return cudaGetLastError() != cudaSuccess ? RFI_ERR_CUDA : RFI_ERR_UNSUPPORTED;
     s.ctas_per_sm = std::min(want_ctas, occ);
+    P->grid_apply = 0;
+    if (P->kmom >= 2) {
+        const int occ_apply = persistent_occupancy(P->bits, kModeApply + P->mode, s);
+        if (occ_apply < 1) return cudaGetLastError() != cudaSuccess ? RFI_ERR_CUDA : RFI_ERR_UNSUPPORTED;
+        P->grid_apply = P->sm_count * occ_apply;  // clamped to the tile count with the grid
+    }
     P->shape = s;
     return RFI_OK;
 }
@@ -84,7 +88,8 @@ rfi_status plan_build_tiles(rfi_plan_s *P) {
     std::vector<Tile> tiles;
     for (int i = 0; i < P->S; ++i) {
         const int64_t wb = static_cast<int64_t>(P->W[i]) * bps;
-        const int64_t per = (wb % 16 == 0) ? std::max<int64_t>(1, P->shape.stage_bytes / wb) : 1;
+        int64_t per = (wb % 16 == 0) ? std::max<int64_t>(1, P->shape.stage_bytes / wb) : 1;
+        if (P->kmom >= 2) per = std::min<int64_t>(per, kApplyTileWindows);
         for (int64_t w0 = 0; w0 < P->nwin[i]; w0 += per) {
             const int64_t nw = std::min<int64_t>(per, P->nwin[i] - w0);
             const int64_t s0 = w0 * P->W[i];
@@ -104,6 +109,7 @@ rfi_status plan_build_tiles(rfi_plan_s *P) {
     P->tiles_host = std::move(tiles);
     P->ntiles = static_cast<int>(P->tiles_host.size());
     P->grid = std::max(1, std::min(P->ntiles, P->sm_count * P->shape.ctas_per_sm));
+    if (P->kmom >= 2) P->grid_apply = std::max(1, std::min(P->ntiles, P->grid_apply));
     return RFI_OK;
 }
 
@@ -180,7 +186,7 @@ rfi_status plan_enqueue_batched(rfi_plan_s *P, cudaStream_t st) {
     RFI_CUDA(launch_mom(P->bits, P->d_mchunks, static_cast<int>(P->mchunks.size()), P->d_mad, P->d_mom, P->kmom,
                         st));
     RFI_CUDA(cudaMemsetAsync(&P->d_ctr->tile_counter, 0, sizeof(unsigned), st));
-    RFI_CUDA(launch_persistent(P->bits, kModeApply + P->mode, P->shape, P->grid, P->d_segs + P->S, P->d_tiles,
+    RFI_CUDA(launch_persistent(P->bits, kModeApply + P->mode, P->shape, P->grid_apply, P->d_segs + P->S, P->d_tiles,
                                P->ntiles, p, &P->d_ctr->tile_counter, 0, st));
     return RFI_OK;
 }

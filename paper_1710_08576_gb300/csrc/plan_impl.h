@@ -42,6 +42,7 @@ struct rfi_plan_s {
     rfi::Shape shape{};
     std::vector<rfi::Tile> tiles_host;
     int ntiles = 0, grid = 0;
+    int grid_apply = 0;  // Median of MAD: grid of the apply pass (no histogram: more CTAs fit)
     // device workspace
     void *ws = nullptr;
     size_t ws_bytes = 0;

@@ -69,3 +69,24 @@ def test_replacement_options_rank_as_reported():
     assert imp[oracle.ZERO] > 3.0
     assert abs(imp[oracle.ZERO] - imp[oracle.NOISE]) < 1.5
     assert imp[oracle.NOISE] > imp[oracle.CLIP] + 3.0
+
+
+def test_library_metric_matches_the_oracle():
+    """rfi_improvement_db (host code of the library, no GPU) against the oracle's metric on
+    interleaved per-window powers: same grouping, same blocks, equal to rounding."""
+    import paper_1710_08576_gb300 as rfi
+    rng = np.random.default_rng(7)
+    nwin = 64 * 37 + 5
+    pu = rng.integers(10 ** 6, 10 ** 7, size=nwin)
+    pf = pu - rng.integers(0, 10 ** 6, size=nwin)
+    pu[100:130] *= 30  # bursts
+    inter = np.empty(2 * nwin, np.uint64)
+    inter[0::2] = pu
+    inter[1::2] = pf
+    for wpp, ppb in ((1, 64), (4, 16), (3, 7)):
+        st, db, su, sf = rfi.rfi_improvement_db(inter, wpp, ppb)
+        assert st == rfi.RFI_OK
+        ref = oracle.improvement_db(pu, pf, wpp, ppb)
+        assert db == pytest.approx(ref[0], rel=1e-9, abs=1e-12)
+        assert su == pytest.approx(ref[1], rel=1e-12) and sf == pytest.approx(ref[2], rel=1e-12)
+    assert rfi.rfi_improvement_db(inter[:20], 1, 64)[0] == rfi.RFI_ERR_INVALID_ARG
