@@ -26,11 +26,14 @@
 // difference, a three-operation byte compare against t, a byte permute that replicates each
 // byte's flag bit into 0x00/0xFF, and a byte dot product that packs the flags into mask bits.
 //
-// Digital-noise replacement is deferred and shared out: the replace pass writes the flagged
-// samples' positions into a per-group list in shared memory, and after one more group barrier
-// all threads of the group evaluate Philox for the list, so neither a lane nor a warp idles
-// while another one runs a long noise loop. A window whose list would overflow hands the rest
-// of its flagged samples to a per-warp path that numbers them across the warp.
+// Digital-noise replacement is deferred and shared out over the group, in one of two ways
+// chosen by sample width for the flag densities each one serves best. int8 (sparse, bursty
+// flags): the replace pass keeps every chunk's flag mask in shared memory; a block scan of
+// the threads' flag counts numbers the flagged samples and each thread evaluates Philox for
+// every T-th of them, found by a binary search. 12-bit (dense flags): the replace pass writes
+// the flagged samples' positions into a per-group list, and after one more group barrier all
+// threads evaluate Philox for the list; a window whose list would overflow hands the rest of
+// its flagged samples to a per-warp path that numbers them across the warp.
 
 #pragma once
 
@@ -238,10 +241,13 @@ struct Shm {
     Ctl *ctl;
     int ncopies;         // 12-bit only
     int bar_id;          // named barrier of this consumer group
-    uint16_t *nlist;     // digital noise: positions of the window's flagged samples (or null)
+    uint16_t *nlist;     // digital noise work area (or null): int8, the window's chunk flag masks;
+                         // 12-bit, the positions of its flagged samples
 };
 
-// Capacity of the digital-noise list and the mark of an entry that was handed to the warp path.
+// Capacity of the digital-noise work area (16-bit entries: int8 chunk masks of windows up to
+// 65536 samples, or 12-bit flagged positions) and the mark of a list entry that was handed to
+// the per-warp path.
 constexpr int kNoiseList = 4096;
 constexpr uint16_t kNoiseSkip = 0xFFFFu;
 
@@ -691,6 +697,48 @@ __device__ __forceinline__ void noise_list(const Shm &sm, const Win &w, const Re
     }
 }
 
+// Digital noise (int8), after the replace pass: thread t has flagged cnt samples in its chunks
+// t, t + T, t + 2T, ... whose masks are in sm.nlist. A block scan gives each thread its first
+// index, so the window's flagged samples are numbered in the order (owner thread, chunk, bit);
+// thread t takes numbers t, t + T, ..., finds each one's owner by a binary search over the
+// first indices (16-bit values in the now idle cumulative-count array: a thread that owns a
+// flagged sample starts below 65536), walks the owner's chunks to the sample and evaluates
+// Philox for it. Every walk is bounded by the window and every store is checked against the
+// window's length.
+template <int T, bool PW>
+__device__ __forceinline__ void noise_deferred8(const Shm &sm, const Win &w, const Rep &r, const Params &p, int tid,
+                                                uint32_t cnt, Pow &pw) {
+    constexpr int NW = T / 32;
+    const uint32_t first = block_offsets<T>(sm, cnt, tid);  // group barrier inside
+    uint32_t total = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) total += sm.ctl->warp_tot[i];
+    uint16_t *firsts = reinterpret_cast<uint16_t *>(sm.cum);
+    firsts[tid] = static_cast<uint16_t>(first < 65535u ? first : 65535u);
+    named_bar(sm.bar_id, T);
+    const int nchunks = (w.n + 15) >> 4;
+    for (uint32_t q = static_cast<uint32_t>(tid); q < total; q += T) {
+        int u = 0;
+#pragma unroll
+        for (int step = T / 2; step >= 1; step >>= 1)
+            if (firsts[u + step] <= q) u += step;
+        uint32_t j = q - firsts[u];
+        int c = u;
+        uint32_t b = sm.nlist[c];
+        while (j >= static_cast<uint32_t>(__popc(b)) && c + T < nchunks) {
+            j -= __popc(b);
+            c += T;
+            b = sm.nlist[c];
+        }
+        if (j >= static_cast<uint32_t>(__popc(b))) continue;
+        const int pos = c * 16 + nth_set_bit(b, static_cast<int>(j));
+        if (pos >= w.n) continue;
+        const int32_t z = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pos, Geo<8>::kLo, Geo<8>::kHi);
+        w.out[pos] = static_cast<uint8_t>(z);
+        if (PW) pw.z += static_cast<uint32_t>(z * z);
+    }
+}
+
 // Sum of squares of the bytes of w kept by keep (0xFF per kept byte), as signed int8 samples.
 __device__ __forceinline__ uint32_t sq4(uint32_t w, uint32_t keep) {
     const int32_t v = static_cast<int32_t>(w & keep);
@@ -739,7 +787,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 if (PW) pw.z += sq4(v.x, ~0u) + sq4(v.y, ~0u) + sq4(v.z, ~0u) + sq4(v.w, ~0u);
                 mk[c] = static_cast<uint16_t>(bits);
                 flagged += __popc(bits);
-                if (MODE == 3) noise_append<8, T, PW>(sm, w, r, p, lane, c, bits, par, pw);
+                if (MODE == 3) sm.nlist[c] = static_cast<uint16_t>(bits);
             }
         }
         // warp-uniform rounds: lane handles chunk base + lane
@@ -786,8 +834,8 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 }
                 flagged += __popc(bits);
                 if (mk) mk[c] = static_cast<uint16_t>(bits);
+                if (MODE == 3) sm.nlist[c] = static_cast<uint16_t>(bits);
             }
-            if (MODE == 3) noise_append<8, T, PW>(sm, w, r, p, lane, c, bits, par, pw);
         }
         if (mk) {
             for (int c = nchunks + tid; c < 2 * w.mask_words; c += T) mk[c] = 0;
@@ -888,8 +936,12 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
     Pow pw = {0u, 0u};
     if (!STATS) f = phase_replace<BITS, RMODE, T, PW>(sm, w, r, p, tid, par, pw);
     if (!STATS && RMODE == 3) {
-        named_bar(sm.bar_id, T);  // every flagged position of the window is in the list
-        noise_list<BITS, T, PW>(sm, w, r, p, tid, par, pw);
+        if (BITS == 8) {
+            noise_deferred8<T, PW>(sm, w, r, p, tid, f, pw);
+        } else {
+            named_bar(sm.bar_id, T);  // every flagged position of the window is in the list
+            noise_list<BITS, T, PW>(sm, w, r, p, tid, par, pw);
+        }
     }
     f = __reduce_add_sync(0xFFFFFFFFu, f);
     unsigned long long px = 0ull, pz = 0ull;
@@ -911,7 +963,7 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
             __threadfence_block();
             const uint32_t cnt = atomicExch(&sm.ctl->count[par], 0u);
             sm.ctl->done[par] = 0u;
-            if (RMODE == 3) sm.ctl->ncount[par] = 0u;  // every warp has read it
+            if (BITS == 12 && RMODE == 3) sm.ctl->ncount[par] = 0u;  // every warp has read it
             if (PW) {
                 const unsigned long long sx = atomicExch(&sm.ctl->pw[par][0], 0ull);
                 const unsigned long long sz = atomicExch(&sm.ctl->pw[par][1], 0ull);

@@ -206,3 +206,31 @@ def test_autotuned_plan(cuda, rfi):
     got, ref, st, _, info = _run_both(rfi, xs, [16384] * 4, 8, 5.0, 2, flags=rfi.RFI_PLAN_AUTOTUNE | 0x4)
     assert st == 0 and info.grid >= 1
     assert_same(got, ref, "autotuned")
+
+
+@pytest.mark.parametrize("bits", [8, 12])
+@pytest.mark.parametrize("form", ["batched", "per_stream"])
+def test_noise_list_overflow(cuda, rfi, bits, form):
+    """Windows whose flagged samples outnumber the digital-noise list (4096 entries): 55 % of
+    each window sits in a narrow core (small D) and 45 % far outside it, so 7000+ of 16384
+    samples take noise; the ones past the list are replaced by the lane that found them. A
+    65536-sample window (listed by no entry) and windows just under the capacity too."""
+    rng = np.random.default_rng(bits)
+    dt = np.int8 if bits == 8 else np.int16
+    far = 100 if bits == 8 else 1500
+
+    def window(n, frac):
+        core = rng.integers(-2, 3, size=n)
+        out = rng.choice([-far, far], size=n) + rng.integers(-3, 4, size=n)
+        pick = rng.random(n) < frac
+        return np.where(pick, out, core).astype(dt)
+
+    W = 16384
+    xs = [np.concatenate([window(W, 0.45) for _ in range(6)]),
+          np.concatenate([window(W, 4000 / W) for _ in range(4)] + [window(123, 0.4)]),
+          window(65536, 0.3)]
+    wins = [W, W, 65536]
+    got, ref, st, totals, _ = _run_both(rfi, xs, wins, bits, 3.0, 3, seed=99, flags=FORMS[form])
+    assert st == 0
+    assert_same(got, ref, "noise overflow %s" % form)
+    assert got[0]["counts"].min() > 4096
