@@ -88,6 +88,8 @@ typedef enum rfi_mode {
 #define RFI_PLAN_BATCHED 0x2u     /* one persistent launch over all windows (default) */
 #define RFI_PLAN_GRAPH 0x4u       /* batched launch replayed from a CUDA graph */
 #define RFI_PLAN_AUTOTUNE 0x8u    /* time candidate launch shapes at create, keep the fastest */
+#define RFI_PLAN_NO_SPLIT 0x20u   /* keep one work list even when window sizes differ widely (see
+                                     rfi_plan_create) */
 #define RFI_PLAN_POWER 0x10u      /* also sum x^2 and z^2 over every window (the detected power of
                                      the unfiltered and filtered signal, rfi_stats_power), for
                                      the improvement metric of Section III-A. Batched form and
@@ -152,7 +154,12 @@ typedef struct rfi_plan_info {
 
 /* Validate desc, copy its arrays, allocate the workspace, build the work list and (with
  * RFI_PLAN_AUTOTUNE) time the candidate launch shapes on scratch buffers. Uses the current
- * CUDA device. Synchronous. */
+ * CUDA device. Synchronous.
+ * A batched plan whose window sizes span more than one stage class (windows of at most 16 KiB,
+ * at most 32 KiB, and larger) is split into one internal plan per class, each with its own
+ * launch shape, work list and graph, run one after the other on the caller's stream; results
+ * are the same bits (RFI_PLAN_NO_SPLIT keeps one work list). rfi_plan_get_info then reports the
+ * sum of tiles and kernels, the largest grid and the shape of the class with the most samples. */
 RFI_API rfi_status rfi_plan_create(const rfi_plan_desc *desc, rfi_plan_t *plan);
 
 /* Excise every stream of the plan: in[s] -> out[s], optional mask[s] and counts[s] (an array

@@ -29,6 +29,7 @@ RFI_PLAN_BATCHED = 0x2
 RFI_PLAN_GRAPH = 0x4
 RFI_PLAN_AUTOTUNE = 0x8
 RFI_PLAN_POWER = 0x10
+RFI_PLAN_NO_SPLIT = 0x20
 RFI_PLAN_INJECT_TIMEOUT = 0x100
 
 

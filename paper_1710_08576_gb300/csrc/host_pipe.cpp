@@ -87,6 +87,20 @@ using namespace rfi;
 extern "C" rfi_status rfi_excise_host(rfi_plan_t P, const void *const *in, void *const *out,
                                       uint32_t *const *mask, uint32_t *const *counts, void *stream) {
     if (!P) return RFI_ERR_INVALID_ARG;
+    if (!P->parts.empty()) {
+        if (!in || !out) return RFI_ERR_INVALID_ARG;
+        for (size_t k = 0; k < P->parts.size(); ++k) {
+            const auto a = part_args<const void *>(P, k, in);
+            const auto b = part_args<void *>(P, k, out);
+            const auto m = part_args<uint32_t *>(P, k, mask);
+            const auto c = part_args<uint32_t *>(P, k, counts);
+            const rfi_status rs = rfi_excise_host(P->parts[k], a.data(), b.data(), mask ? m.data() : nullptr,
+                                                  counts ? c.data() : nullptr, stream);
+            if (rs != RFI_OK) return rs;
+        }
+        P->last_windows = P->total_windows;
+        return RFI_OK;
+    }
     if (P->kmom >= 2) return RFI_ERR_UNSUPPORTED;  // Eq. 3 needs every earlier window's MAD
     if (P->power) return RFI_ERR_UNSUPPORTED;      // the chunk kernels do not meter power
     rfi_status rs = plan_check_buffers(P, in, out, mask, counts);

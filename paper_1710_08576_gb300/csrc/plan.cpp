@@ -292,7 +292,7 @@ rfi_status rfi_plan_create(const rfi_plan_desc *d, rfi_plan_t *out_plan) {
     if (!(d->k > 0.0) || !std::isfinite(d->k) || d->k > 1.0e6) return RFI_ERR_INVALID_ARG;
     if (d->mode < RFI_REPLACE_ZERO || d->mode > RFI_REPLACE_NOISE) return RFI_ERR_INVALID_ARG;
     const uint32_t known = RFI_PLAN_PER_STREAM | RFI_PLAN_BATCHED | RFI_PLAN_GRAPH | RFI_PLAN_AUTOTUNE |
-                           RFI_PLAN_INJECT_TIMEOUT | RFI_PLAN_POWER;
+                           RFI_PLAN_INJECT_TIMEOUT | RFI_PLAN_POWER | RFI_PLAN_NO_SPLIT;
     if (d->flags & ~known) return RFI_ERR_INVALID_ARG;
     if ((d->flags & RFI_PLAN_PER_STREAM) && (d->flags & (RFI_PLAN_BATCHED | RFI_PLAN_GRAPH)))
         return RFI_ERR_INVALID_ARG;
@@ -349,6 +349,44 @@ rfi_status rfi_plan_create(const rfi_plan_desc *d, rfi_plan_t *out_plan) {
         delete P;
         return RFI_ERR_CUDA;
     }
+    // windows of very different sizes: one internal plan per stage class
+    if (!(P->flags & (RFI_PLAN_PER_STREAM | RFI_PLAN_NO_SPLIT))) {
+        const int bps = P->bits == 8 ? 1 : 2;
+        std::vector<std::vector<int>> cls(3);
+        for (int i = 0; i < P->S; ++i)
+            cls[window_class(std::min<int64_t>(P->W[i], P->len[i]) * bps)].push_back(i);
+        int nonempty = 0;
+        for (auto &c : cls) nonempty += c.empty() ? 0 : 1;
+        if (nonempty > 1) {
+            for (auto &c : cls) {
+                if (c.empty()) continue;
+                std::vector<int64_t> len;
+                std::vector<int32_t> W;
+                std::vector<uint32_t> sid;
+                for (int i : c) {
+                    len.push_back(P->len[i]);
+                    W.push_back(P->W[i]);
+                    sid.push_back(P->sid[i]);
+                }
+                rfi_plan_desc cd = *d;
+                cd.num_streams = static_cast<int32_t>(c.size());
+                cd.stream_len = len.data();
+                cd.window_len = W.data();
+                cd.stream_id = sid.data();
+                cd.flags = d->flags | RFI_PLAN_NO_SPLIT;
+                rfi_plan_t child = nullptr;
+                rs = rfi_plan_create(&cd, &child);
+                if (rs != RFI_OK) {
+                    rfi_plan_destroy(P);
+                    return rs;
+                }
+                P->parts.push_back(child);
+                P->part_streams.push_back(c);
+            }
+            *out_plan = P;
+            return RFI_OK;
+        }
+    }
     rs = plan_choose_shape(P, d->shape);
     if (rs == RFI_OK) rs = plan_build_tiles(P);
     if (rs == RFI_OK) rs = plan_alloc_workspace(P);
@@ -367,6 +405,20 @@ rfi_status rfi_plan_create(const rfi_plan_desc *d, rfi_plan_t *out_plan) {
 rfi_status rfi_excise(rfi_plan_t P, const void *const *in, void *const *out, uint32_t *const *mask,
                       uint32_t *const *counts, void *stream) {
     if (!P) return RFI_ERR_INVALID_ARG;
+    if (!P->parts.empty()) {
+        if (!in || !out) return RFI_ERR_INVALID_ARG;
+        for (size_t k = 0; k < P->parts.size(); ++k) {
+            const auto a = part_args<const void *>(P, k, in);
+            const auto b = part_args<void *>(P, k, out);
+            const auto m = part_args<uint32_t *>(P, k, mask);
+            const auto c = part_args<uint32_t *>(P, k, counts);
+            const rfi_status rs = rfi_excise(P->parts[k], a.data(), b.data(), mask ? m.data() : nullptr,
+                                             counts ? c.data() : nullptr, stream);
+            if (rs != RFI_OK) return rs;
+        }
+        P->last_windows = P->total_windows;
+        return RFI_OK;
+    }
     rfi_status rs = plan_check_buffers(P, in, out, mask, counts);
     if (rs != RFI_OK) return rs;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -398,6 +450,24 @@ rfi_status rfi_excise(rfi_plan_t P, const void *const *in, void *const *out, uin
 
 rfi_status rfi_stats(rfi_plan_t P, int32_t *const *median, int32_t *const *mad, rfi_totals *totals, void *stream) {
     if (!P) return RFI_ERR_INVALID_ARG;
+    if (!P->parts.empty()) {
+        rfi_totals sum{0, 0, RFI_OK};
+        rfi_status dev = RFI_OK;
+        for (size_t k = 0; k < P->parts.size(); ++k) {
+            const auto a = part_args<int32_t *>(P, k, median);
+            const auto b = part_args<int32_t *>(P, k, mad);
+            rfi_totals t{};
+            const rfi_status rs = rfi_stats(P->parts[k], median ? a.data() : nullptr, mad ? b.data() : nullptr, &t,
+                                            stream);
+            if (rs == RFI_ERR_INVALID_ARG || rs == RFI_ERR_CUDA) return rs;
+            if (dev == RFI_OK && rs != RFI_OK) dev = rs;
+            sum.windows += t.windows;
+            sum.flagged += t.flagged;
+        }
+        sum.device_status = dev;
+        if (totals) *totals = sum;
+        return dev;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     for (int i = 0; i < P->S; ++i) {
         const size_t b = sizeof(int32_t) * P->nwin[i];
@@ -423,6 +493,14 @@ rfi_status rfi_stats(rfi_plan_t P, int32_t *const *median, int32_t *const *mad, 
 
 rfi_status rfi_stats_mom(rfi_plan_t P, int32_t *const *mom, void *stream) {
     if (!P) return RFI_ERR_INVALID_ARG;
+    if (!P->parts.empty()) {
+        for (size_t k = 0; k < P->parts.size(); ++k) {
+            const auto a = part_args<int32_t *>(P, k, mom);
+            const rfi_status rs = rfi_stats_mom(P->parts[k], mom ? a.data() : nullptr, stream);
+            if (rs != RFI_OK) return rs;
+        }
+        return RFI_OK;
+    }
     if (P->kmom < 2) return RFI_ERR_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     for (int i = 0; i < P->S; ++i)
@@ -434,6 +512,14 @@ rfi_status rfi_stats_mom(rfi_plan_t P, int32_t *const *mom, void *stream) {
 
 rfi_status rfi_stats_power(rfi_plan_t P, uint64_t *const *power, void *stream) {
     if (!P) return RFI_ERR_INVALID_ARG;
+    if (!P->parts.empty()) {
+        for (size_t k = 0; k < P->parts.size(); ++k) {
+            const auto a = part_args<uint64_t *>(P, k, power);
+            const rfi_status rs = rfi_stats_power(P->parts[k], power ? a.data() : nullptr, stream);
+            if (rs != RFI_OK) return rs;
+        }
+        return RFI_OK;
+    }
     if (!P->power) return RFI_ERR_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     for (int i = 0; i < P->S; ++i)
@@ -483,6 +569,26 @@ rfi_status rfi_improvement_db(const uint64_t *power, int64_t nwin, int32_t windo
 rfi_status rfi_plan_get_info(rfi_plan_t P, rfi_plan_info *info) {
     if (!P || !info) return RFI_ERR_INVALID_ARG;
     std::memset(info, 0, sizeof(*info));
+    if (!P->parts.empty()) {
+        uint64_t most = 0;
+        for (rfi_plan_s *c : P->parts) {
+            rfi_plan_info ci;
+            rfi_plan_get_info(c, &ci);
+            info->workspace_bytes += ci.workspace_bytes;
+            info->tiles += ci.tiles;
+            info->grid = std::max(info->grid, ci.grid);
+            info->kernels_per_call += ci.kernels_per_call;
+            if (ci.total_samples > most) {
+                most = ci.total_samples;
+                info->shape = ci.shape;
+            }
+        }
+        info->k_q16 = P->kq;
+        info->total_windows = P->total_windows;
+        info->total_samples = P->total_samples;
+        info->sm_count = P->sm_count;
+        return RFI_OK;
+    }
     info->k_q16 = P->kq;
     info->total_windows = P->total_windows;
     info->total_samples = P->total_samples;
@@ -503,6 +609,7 @@ rfi_status rfi_plan_get_info(rfi_plan_t P, rfi_plan_info *info) {
 
 rfi_status rfi_plan_destroy(rfi_plan_t P) {
     if (!P) return RFI_OK;
+    for (rfi_plan_s *c : P->parts) rfi_plan_destroy(c);
     plan_release_host_pipe(P);
     if (P->gexec) cudaGraphExecDestroy(P->gexec);
     if (P->graph) cudaGraphDestroy(P->graph);

@@ -65,6 +65,9 @@ struct rfi_plan_s {
     cudaGraphExec_t gexec = nullptr;
     rfi::HostPipe pipe;
     size_t host_pipe_bytes = 0;
+    // a plan split by window-size class: one internal plan per class and its stream indices
+    std::vector<rfi_plan_s *> parts;
+    std::vector<std::vector<int>> part_streams;
 };
 
 namespace rfi {
@@ -82,6 +85,15 @@ std::vector<Seg> plan_segs(const rfi_plan_s *P, const void *const *in, void *con
 rfi_status plan_check_buffers(const rfi_plan_s *P, const void *const *in, void *const *out,
                               uint32_t *const *mask, uint32_t *const *counts);
 inline int plan_nsegs(const rfi_plan_s *P) { return P->kmom >= 2 ? 2 * P->S : P->S; }
+// Stage class of a window of wb bytes: 0 up to 16 KiB, 1 up to 32 KiB, 2 larger.
+inline int window_class(int64_t wb) { return wb <= 16384 ? 0 : (wb <= 32768 ? 1 : 2); }
+// Per-part pointer arrays of a split plan (entries in the part's stream order).
+template <class T>
+std::vector<T> part_args(const rfi_plan_s *P, size_t k, T const *all) {
+    std::vector<T> v;
+    for (int i : P->part_streams[k]) v.push_back(all ? all[i] : T());
+    return v;
+}
 // Kernel mode of a per-window MAD plan (the power-metered form when RFI_PLAN_POWER is set).
 inline int plan_kernel_mode(const rfi_plan_s *P) { return P->mode | (P->power ? kModePower : 0); }
 

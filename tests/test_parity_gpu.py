@@ -234,3 +234,41 @@ def test_noise_list_overflow(cuda, rfi, bits, form):
     assert st == 0
     assert_same(got, ref, "noise overflow %s" % form)
     assert got[0]["counts"].min() > 4096
+
+
+@pytest.mark.parametrize("mode", [0, 3])
+def test_split_plan_by_window_class(cuda, rfi, mode):
+    """Streams whose windows span the three stage classes (<= 16 KiB, <= 32 KiB, larger) run as
+    one internal plan per class: outputs, per-stream M and D and the totals equal the single
+    work list and the oracle; the graph, host-buffer and MoM forms route the same way."""
+    import torch
+    windows = [1024, 65536, 4096, 32768, 16384, 20000, 60000]
+    lens = [40 * w + (w // 3) for w in windows]
+    p = synth.params(seed=11, sigma=16.0, burst_rate=2e-3, burst_len_max=64, bits=8)
+    xs = [synth.fill(p, s, n) for s, n in enumerate(lens)]
+    sids = [100 + i for i in range(len(xs))]
+    ref = oracle_run(xs, windows, 8, 3.0, mode, 0, 5, sids)
+    for flags in (0, rfi.RFI_PLAN_GRAPH, rfi.RFI_PLAN_NO_SPLIT):
+        got, st, totals, info = gpu_run(rfi, xs, windows, 8, 3.0, mode, 0, 5, flags=flags, stream_ids=sids)
+        assert st == 0
+        assert_same(got, ref, "split flags %d" % flags)
+        assert totals.flagged == sum(int(r["counts"].sum()) for r in ref)
+        assert totals.windows == sum(-(-n // w) for n, w in zip(lens, windows))
+        assert info.kernels_per_call == (1 if flags & rfi.RFI_PLAN_NO_SPLIT else 3)
+    got, st, _, _ = gpu_run(rfi, xs, windows, 8, 3.0, mode, 0, 5, stream_ids=sids, host=True)
+    assert st == 0
+    assert_same(got, ref, "split host pipeline")
+    # a MoM plan splits the same way (the median of MADs stays within each stream)
+    plan = rfi.Plan(8, lens, windows, 3.0, mode, 0, 5, 0, sids, mom_windows=5)
+    try:
+        ins = [torch.from_numpy(x).cuda() for x in xs]
+        outs = [torch.empty_like(t) for t in ins]
+        plan.excise(ins, outs)
+        moms = [torch.zeros(n, dtype=torch.int32, device="cuda") for n in plan.num_windows]
+        plan.stats_mom(moms)
+        torch.cuda.synchronize()
+        for i, x in enumerate(xs):
+            r = oracle.excise_mom(x, windows[i], 3.0, mode, 5, seed=5, stream_id=sids[i], threads=8)
+            assert np.array_equal(outs[i].cpu().numpy(), r["z"]) and np.array_equal(moms[i].cpu().numpy(), r["mom"])
+    finally:
+        plan.close()
