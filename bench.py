@@ -334,6 +334,42 @@ def run_ours(args):
         mplan.close()
         del mmask, mcnt
 
+    # digital copy (Section III-A): the 8 variants of the step in one pass, each to its own buffers
+    copies = None
+    if not args.no_copies and args.workload == "gwb60":
+        V = len(w.variants)
+        cplan = rfi.CopiesPlan(8, lens, Ws, [(v.k, v.mode, v.const, v.seed) for v in w.variants],
+                               rfi.RFI_PLAN_GRAPH, sids)
+        c_out = [[torch.empty_like(t) for t in dev_in] for _ in range(V)]
+        c_mask = [[torch.empty(mw, dtype=torch.int32, device=dev) for mw in mwords] for _ in range(V)]
+        c_cnt = [[torch.empty(nw, dtype=torch.int32, device=dev) for nw in nwin] for _ in range(V)]
+        csteps = max(1, min(args.steps, 20))
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                cplan.excise(dev_in, c_out, c_mask, c_cnt, stream)
+            stream.synchronize()
+            barrier()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            for _ in range(csteps):
+                cplan.excise(dev_in, c_out, c_mask, c_cnt, stream)
+            c1.record(stream)
+            stream.synchronize()
+        cst, _ = cplan.stats(stream=stream)
+        if cst != 0:
+            raise RuntimeError("digital copy device status %s" % rfi.rfi_status_string(cst))
+        c_ms = max_over_ranks(c0.elapsed_time(c1)) / csteps
+        c_bytes = samples_per_call * (1 + V * (1 + 1 / 8)) + windows_per_call * (8 + 4 * V)
+        copies = {"value": sum_over_ranks(samples_per_call * V) / (c_ms * 1e-3) / 1e9, "unit": UNIT,
+                  "ms_per_step": c_ms, "steps": csteps, "variants": V, "launches_per_step": 1,
+                  "achieved_gbs": c_bytes / (c_ms * 1e-3) / 1e9,
+                  "frac": c_bytes / (c_ms * 1e-3) / 1e9 / peak,
+                  "bytes_rule": "per sample 1 read + per variant (1 write + 1/8 mask); per window 8 M/D + "
+                                "4 count per variant",
+                  "form": "persistent kernel, one histogram per window, the 8 variants' outputs from it"}
+        cplan.close()
+        del c_out, c_mask, c_cnt
+
     # end to end through rfi_excise_host with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -400,6 +436,7 @@ def run_ours(args):
                          "kernel": "persistent_kernel<%d,mode,cw,g>" % bits},
             "cpu_baseline": cpu,
             "mom": mom,
+            "digital_copy": copies,
             "e2e": e2e,
             "gpu_launches": len(batched) * args.steps,
             "gpu_launches_note": "persistent-kernel launches in the timed region of `value`",
@@ -610,6 +647,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mom", action="store_true")
+    ap.add_argument("--no-copies", action="store_true")
     ap.add_argument("--workload", choices=["gwb60", "twelve60", "uneven60", "serve60"], default="gwb60")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--feed", choices=["device", "host"], default="device")

@@ -182,6 +182,29 @@ RFI_API rfi_status rfi_excise_host(rfi_plan_t plan, const void *const *in, void 
 RFI_API rfi_status rfi_stats(rfi_plan_t plan, int32_t *const *median, int32_t *const *mad,
                      rfi_totals *totals, void *stream);
 
+/* Digital copy (Section III-A: one input filtered with several threshold multiples and
+ * replacement options at once, the FPGA's 1:4 copy mode). A plan for up to RFI_MAX_COPIES
+ * variants of (k, mode, const_value, seed); desc gives the streams, windows, stream ids and
+ * flags (its k, mode, const_value and seed are not used). One pass stages each window once,
+ * estimates its median and MAD once and writes every variant's outputs; each variant's output
+ * equals a plain plan's with its parameters. Batched form only (RFI_PLAN_PER_STREAM,
+ * RFI_PLAN_POWER and mom_windows >= 2 return RFI_ERR_UNSUPPORTED); fixed launch shape;
+ * rfi_excise on such a plan returns RFI_ERR_INVALID_ARG. rfi_stats gives the shared median
+ * and MAD and, in totals, the flagged samples of all variants. */
+#define RFI_MAX_COPIES 8
+typedef struct rfi_variant {
+    double k;
+    int32_t mode;
+    int32_t const_value;
+    uint64_t seed;
+} rfi_variant;
+RFI_API rfi_status rfi_plan_create_copies(const rfi_plan_desc *desc, int32_t nvariants, const rfi_variant *variants,
+                                          rfi_plan_t *plan);
+/* in: [S] as rfi_excise; out, mask, counts: [nvariants * S], variant-major (entry v * S + s is
+ * variant v of stream s); mask and counts (and their elements) may be NULL. Asynchronous. */
+RFI_API rfi_status rfi_excise_copies(rfi_plan_t plan, const void *const *in, void *const *out,
+                                     uint32_t *const *mask, uint32_t *const *counts, void *stream);
+
 /* Median-of-MAD plans (mom_windows >= 2): the dispersion each window of the last rfi_excise
  * used, the lower median of the MADs of the mom_windows windows ending at it (Eq. 3), into
  * caller device arrays of nwin(s) int32 (array pointer or element may be NULL). Asynchronous

@@ -50,6 +50,11 @@ class RfiPlanDesc(ctypes.Structure):
                 ("mom_windows", ctypes.c_int32)]
 
 
+class RfiVariant(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("mode", ctypes.c_int32), ("const_value", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
 class RfiTotals(ctypes.Structure):
     _fields_ = [("windows", ctypes.c_uint64), ("flagged", ctypes.c_uint64),
                 ("device_status", ctypes.c_int32)]
@@ -109,6 +114,9 @@ def _load():
         "rfi_excise_host": (ctypes.c_int, [_P, _PP, _PP, _PP, _PP, _P]),
         "rfi_stats": (ctypes.c_int, [_P, _PP, _PP, ctypes.POINTER(RfiTotals), _P]),
         "rfi_stats_mom": (ctypes.c_int, [_P, _PP, _P]),
+        "rfi_plan_create_copies": (ctypes.c_int, [ctypes.POINTER(RfiPlanDesc), ctypes.c_int32,
+                                                  ctypes.POINTER(RfiVariant), ctypes.POINTER(_P)]),
+        "rfi_excise_copies": (ctypes.c_int, [_P, _PP, _PP, _PP, _PP, _P]),
         "rfi_stats_power": (ctypes.c_int, [_P, _PP, _P]),
         "rfi_improvement_db": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int64, ctypes.c_int32,
                                               ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
@@ -519,3 +527,28 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class CopiesPlan(Plan):
+    """A digital-copy plan (rfi_plan_create_copies): one pass, several (k, mode, const, seed)
+    variants; outputs are given per variant (lists of per-stream buffers)."""
+
+    def __init__(self, bits, stream_len, window_len, variants, flags=0, stream_id=None, shape=None):
+        self.desc = make_desc(bits, stream_len, window_len, 3.0, 0, 0, 0, flags, stream_id, shape)
+        n = len(variants)
+        self._vars = (RfiVariant * n)(*[RfiVariant(float(v[0]), int(v[1]), int(v[2]), int(v[3])) for v in variants])
+        h = ctypes.c_void_p()
+        check(LIB.rfi_plan_create_copies(ctypes.byref(self.desc), n, self._vars, ctypes.byref(h)),
+              "rfi_plan_create_copies")
+        self.handle = h.value
+        self.bits = bits
+        self.stream_len = [int(v) for v in stream_len]
+        self.window_len = [int(v) for v in window_len]
+        self.nvariants = n
+
+    def excise(self, ins, outs, masks=None, counts=None, stream=None):
+        """outs / masks / counts: one list of per-stream buffers per variant (None entries allowed)."""
+        flat = lambda per_var: None if per_var is None else [b for lst in per_var for b in lst]  # noqa: E731
+        a, b, c, d = _ptr_array(ins), _ptr_array(flat(outs)), _ptr_array(flat(masks)), _ptr_array(flat(counts))
+        check(LIB.rfi_excise_copies(self.handle, a[0], b[0], c[0] if c else None, d[0] if d else None,
+                                    _stream(stream)), "rfi_excise_copies")

@@ -242,7 +242,7 @@ rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req) {
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return RFI_ERR_CUDA;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    Params p;
+    Params p{};
     p.kq = P->kq;
     p.seed = P->seed;
     p.cval = P->cval;

@@ -144,9 +144,22 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 // ------------------------------------------------------------------ Philox4x32-10 noise
 // Philox4x32-10 as defined by Salmon, Moraes, Dror and Shaw (SC'11): ten rounds; in each the
 // words 0 and 2 are multiplied by the two round multipliers, the high product halves are
-// xor-ed with words 1 and 3 and with the round key. The round keys (the key advanced by two
-// Weyl increments per round) come precomputed in rk0 / rk1.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t *rk0, const uint32_t *rk1) {
+// xor-ed with words 1 and 3 and with the round key. Round r uses the key advanced by r Weyl
+// increments, which a key source gives: precomputed in the kernel parameters (KeysPre), or
+// derived from the seed on the fly (KeysSeed, for the per-variant seeds of a digital copy).
+struct KeysPre {
+    const Params &p;  // the kernel's own parameters: indexed with constants, read in place
+    __device__ __forceinline__ uint32_t a(int r) const { return p.rk0[r]; }
+    __device__ __forceinline__ uint32_t b(int r) const { return p.rk1[r]; }
+};
+struct KeysSeed {
+    uint32_t s0, s1;
+    __device__ __forceinline__ uint32_t a(int r) const { return s0 + static_cast<uint32_t>(r) * 0x9E3779B9u; }
+    __device__ __forceinline__ uint32_t b(int r) const { return s1 + static_cast<uint32_t>(r) * 0xBB67AE85u; }
+};
+
+template <class K>
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const K &key) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         // one 32 x 32 -> 64-bit product per multiplier gives both halves
@@ -154,7 +167,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t *rk0, con
         const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
         const uint32_t lo0 = static_cast<uint32_t>(p0), hi0 = static_cast<uint32_t>(p0 >> 32);
         const uint32_t lo1 = static_cast<uint32_t>(p1), hi1 = static_cast<uint32_t>(p1 >> 32);
-        c = make_uint4(hi1 ^ c.y ^ rk0[r], lo1, hi0 ^ c.w ^ rk1[r], lo0);
+        c = make_uint4(hi1 ^ c.y ^ key.a(r), lo1, hi0 ^ c.w ^ key.b(r), lo0);
     }
     return c;
 }
@@ -163,12 +176,13 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t *rk0, con
 // S2 = 2 * (sum of the eight 16-bit halves of the Philox output) - 8 * 65535.
 // |S2| <= 524280 and sigq < 2^29, so |S2| * sigq < 2^48; dividing by 2^16 first and then by
 // 107020 equals one floor division by their product.
-__device__ __forceinline__ int32_t noise_value(int32_t M, uint32_t sigq, const Params &p, uint32_t sid,
+template <class K>
+__device__ __forceinline__ int32_t noise_value(int32_t M, uint32_t sigq, const K &key, uint32_t sid,
                                                int64_t idx, int32_t lo, int32_t hi) {
     const uint4 r = philox4x32_10(
         make_uint4(static_cast<uint32_t>(idx), static_cast<uint32_t>(static_cast<uint64_t>(idx) >> 32),
                    sid, 0u),
-        p.rk0, p.rk1);
+        key);
     // sum of the eight 16-bit halves: each dp2a adds both halves of one word (weights 1, 1)
     const uint32_t s = __dp2a_lo(r.x, 0x0101u, __dp2a_lo(r.y, 0x0101u, __dp2a_lo(r.z, 0x0101u,
                                                                               __dp2a_lo(r.w, 0x0101u, 0u))));
@@ -210,7 +224,16 @@ struct __align__(16) RepShared {
     uint32_t sigq, active, pad;
     // int8 replace constants (see Rep8)
     uint32_t mb4, tlo7, tsmall, c4, hi4, lo4, ulo7, usmall;
-    uint32_t unone, pad2[3];
+    uint32_t unone;
+    int32_t cval;  // constant replacement (saturated)
+    uint32_t pad2[2];
+};
+
+// Digital copy only (its own region, so that other kernels keep their shared-memory size).
+struct CopyShared {
+    RepShared vrep[kMaxCopies];        // threshold and replacement values per variant
+    uint32_t vcount[kMaxCopies][2];    // flagged samples, by variant and window parity
+    uint32_t ncount[2 * kMaxCopies];   // 12-bit digital-noise list entries, by variant and parity
 };
 
 struct Ctl {
@@ -219,7 +242,7 @@ struct Ctl {
     uint32_t count[2];   // flagged samples, by window parity
     uint32_t done[2];    // warps finished with the window, by window parity
     uint32_t err[2];     // 12-bit range error seen in the window, by window parity
-    uint32_t ncount[2];  // digital-noise list entries, by window parity
+    uint32_t ncount[2];  // 12-bit digital-noise list entries, by window parity
     unsigned long long pw[2][2];  // power-metered excision: {sum x^2, sum z^2}, by window parity
     uint32_t abort;      // set when any warp gave up on a bounded wait
     int32_t mb;          // median bin of the current window (written by its owner thread)
@@ -241,6 +264,7 @@ struct Shm {
     Ctl *ctl;
     int ncopies;         // 12-bit only
     int bar_id;          // named barrier of this consumer group
+    CopyShared *cp;      // digital copy: per-variant state (or null)
     uint16_t *nlist;     // digital noise work area (or null): int8, the window's chunk flag masks;
                          // 12-bit, the positions of its flagged samples
 };
@@ -464,6 +488,7 @@ __device__ __forceinline__ int warp_search(int lane, Pred pred) {
 
 struct Rep {
     int32_t M, D;
+    int32_t cval;     // constant replacement (saturated)
     int32_t t;        // min(ceil(Kq*D / 2^16), sample span + 1)
     int32_t hiv, lov; // threshold replacement above / below (saturated)
     uint32_t sigq;    // 97164 * D
@@ -491,6 +516,7 @@ __device__ __forceinline__ RepShared make_rep(int32_t M, int32_t d, int64_t kq, 
     r.sigq = 97164u * static_cast<uint32_t>(d);
     r.active = (d > 0 && t <= SPAN) ? 1u : 0u;  // |x - M| never exceeds the sample span
     r.pad = 0u;
+    r.cval = cval;
     if (BITS == 8) {
         const uint32_t tt = static_cast<uint32_t>(r.t > 255 ? 255 : r.t);
         const uint32_t ub = static_cast<uint32_t>(r.M + 129);  // smallest biased value above M
@@ -524,11 +550,11 @@ __device__ __forceinline__ void phase_search(const Shm &sm, int n, int lane, int
     if (lane == 0) sm.ctl->rep = make_rep<BITS>(mb - Geo<BITS>::kOffset, d, kq, cval);
 }
 
-__device__ __forceinline__ Rep load_rep(const Ctl *ctl) {
-    const RepShared s = ctl->rep;
+__device__ __forceinline__ Rep load_rep(const RepShared &s) {
     Rep r;
     r.M = s.M;
     r.D = s.D;
+    r.cval = s.cval;
     r.t = s.t;
     r.hiv = s.hiv;
     r.lov = s.lov;
@@ -606,8 +632,8 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int j) {
 // that owns it and a popcount search for its bit, and all 32 lanes evaluate Philox together.
 // The stores go straight to the output; they follow the chunks' own stores in warp order
 // (__syncwarp before the call).
-template <int BITS, int T, bool PW>
-__device__ __forceinline__ void noise_batch(const Win &w, const Rep &r, const Params &p, int lane, int c0,
+template <int BITS, int T, bool PW, class K>
+__device__ __forceinline__ void noise_batch(const Win &w, const Rep &r, const K &p, int lane, int c0,
                                             uint64_t nb, Pow &pw) {
     constexpr int CS = Geo<BITS>::kChunkSamples;
     const uint32_t lo = static_cast<uint32_t>(nb), hi = static_cast<uint32_t>(nb >> 32);
@@ -653,9 +679,9 @@ __device__ __forceinline__ void noise_batch(const Win &w, const Rep &r, const Pa
 // 65536 samples (position 65535 would equal the skip mark) and rounds that do not fit in the
 // list take the per-warp path at once; list entries reserved beyond the written ones are
 // marked skipped. Called by all lanes of the warp with the round's chunk c and flag bits.
-template <int BITS, int T, bool PW>
-__device__ __forceinline__ void noise_append(const Shm &sm, const Win &w, const Rep &r, const Params &p, int lane,
-                                             int c, uint32_t bits, int par, Pow &pw) {
+template <int BITS, int T, bool PW, class K>
+__device__ __forceinline__ void noise_append(const Shm &sm, const Win &w, const Rep &r, const K &p, int lane,
+                                             int c, uint32_t bits, uint32_t *nlc, Pow &pw) {
     constexpr int CS = Geo<BITS>::kChunkSamples;
     if (!__any_sync(0xFFFFFFFFu, bits != 0u)) return;
     const uint32_t cnt = __popc(bits);
@@ -668,7 +694,7 @@ __device__ __forceinline__ void noise_append(const Shm &sm, const Win &w, const 
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
     const bool listed = sm.nlist != nullptr && w.n < 65536;
     uint32_t base = kNoiseList;
-    if (listed && lane == 31) base = atomicAdd(&sm.ctl->ncount[par], total);
+    if (listed && lane == 31) base = atomicAdd(nlc, total);
     base = __shfl_sync(0xFFFFFFFFu, base, 31);
     if (base + total <= static_cast<uint32_t>(kNoiseList)) {
         uint32_t off = base + inc - cnt;
@@ -677,16 +703,16 @@ __device__ __forceinline__ void noise_append(const Shm &sm, const Win &w, const 
     }
     for (uint32_t i = base + lane; i < static_cast<uint32_t>(kNoiseList); i += 32) sm.nlist[i] = kNoiseSkip;
     __syncwarp();  // the round's chunk stores come first
-    noise_batch<BITS, T, PW>(w, r, p, lane, c, static_cast<uint64_t>(bits), pw);
+    noise_batch<BITS, T, PW, K>(w, r, p, lane, c, static_cast<uint64_t>(bits), pw);
 }
 
 // Digital noise, after the group barrier that follows the replace pass: every thread of the
 // group evaluates Philox for a share of the list and stores the value over the chunk's output.
-template <int BITS, int T, bool PW>
-__device__ __forceinline__ void noise_list(const Shm &sm, const Win &w, const Rep &r, const Params &p, int tid,
-                                           int par, Pow &pw) {
+template <int BITS, int T, bool PW, class K>
+__device__ __forceinline__ void noise_list(const Shm &sm, const Win &w, const Rep &r, const K &p, int tid,
+                                           uint32_t *nlc, Pow &pw) {
     if (sm.nlist == nullptr) return;
-    const uint32_t n = min(sm.ctl->ncount[par], static_cast<uint32_t>(kNoiseList));
+    const uint32_t n = min(*nlc, static_cast<uint32_t>(kNoiseList));
     for (uint32_t i = static_cast<uint32_t>(tid); i < n; i += T) {
         const uint32_t pos = sm.nlist[i];
         if (pos == kNoiseSkip) continue;
@@ -705,8 +731,8 @@ __device__ __forceinline__ void noise_list(const Shm &sm, const Win &w, const Re
 // flagged sample starts below 65536), walks the owner's chunks to the sample and evaluates
 // Philox for it. Every walk is bounded by the window and every store is checked against the
 // window's length.
-template <int T, bool PW>
-__device__ __forceinline__ void noise_deferred8(const Shm &sm, const Win &w, const Rep &r, const Params &p, int tid,
+template <int T, bool PW, class K>
+__device__ __forceinline__ void noise_deferred8(const Shm &sm, const Win &w, const Rep &r, const K &p, int tid,
                                                 uint32_t cnt, Pow &pw) {
     constexpr int NW = T / 32;
     const uint32_t first = block_offsets<T>(sm, cnt, tid);  // group barrier inside
@@ -745,9 +771,10 @@ __device__ __forceinline__ uint32_t sq4(uint32_t w, uint32_t keep) {
     return static_cast<uint32_t>(__dp4a(v, v, 0));
 }
 
-template <int BITS, int MODE, int T, bool PW>
-__device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, const Rep &r, const Params &p,
-                                                  int tid, int par, Pow &pw) {
+// rsrc: the shared record r was loaded from (its int8 constants are read from there).
+template <int BITS, int MODE, int T, bool PW, class K>
+__device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, const Rep &r, const K &p,
+                                                  int tid, uint32_t *nlc, Pow &pw, const RepShared *rsrc) {
     constexpr int BPS = Geo<BITS>::kBps;
     const int lane = tid & 31, warp = tid >> 5;
     const int nbytes = w.n * BPS;
@@ -756,7 +783,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
     const uint4 *d4 = reinterpret_cast<const uint4 *>(w.data);
     uint32_t flagged = 0;
     if (BITS == 8) {
-        const uint4 *rq = reinterpret_cast<const uint4 *>(&sm.ctl->rep);
+        const uint4 *rq = reinterpret_cast<const uint4 *>(rsrc);
         const uint4 q2 = rq[2], q3 = rq[3], q4 = rq[4];
         Rep8 k;
         k.mb4 = q2.x;
@@ -859,7 +886,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                     int32_t zo = x;
                     if (fl) {
                         int32_t z = 0;
-                        if (MODE == 1) z = p.cval;
+                        if (MODE == 1) z = r.cval;
                         else if (MODE == 2) z = x > r.M ? r.hiv : r.lov;
                         ww[j >> 1] = (ww[j >> 1] & ~(0xFFFFu << sh)) | ((static_cast<uint32_t>(z) & 0xFFFFu) << sh);
                         bits |= 1u << j;
@@ -881,7 +908,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 }
                 if (mk) mk[c] = static_cast<uint8_t>(bits);
             }
-            if (MODE == 3) noise_append<12, T, PW>(sm, w, r, p, lane, c, bits, par, pw);
+            if (MODE == 3) noise_append<12, T, PW, K>(sm, w, r, p, lane, c, bits, nlc, pw);
         }
         if (mk) {
             for (int c = nchunks + tid; c < 4 * w.mask_words; c += T) mk[c] = 0;
@@ -908,11 +935,12 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
 template <int BITS, int MODE, int T, int ROWB>
 __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64_t widx, const Params &p,
                                int tid, int par, uint32_t release_bar, bool stage_ok, RowSums &rs,
-                               const int2 *amd = nullptr) {
+                               const int2 *amd = nullptr, const Seg *vsegs = nullptr) {
     constexpr int NW = T / 32;
     constexpr bool STATS = (MODE & kModeStats) != 0;
     constexpr bool APPLY = (MODE & kModeApply) != 0;
     constexpr bool PW = (MODE & kModePower) != 0;
+    constexpr bool COPIES = (MODE & kModeCopies) != 0;
     constexpr int RMODE = MODE & 3;
     const int lane = tid & 31;
     if (!APPLY) {
@@ -931,16 +959,55 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
         }
     }
     named_bar(sm.bar_id, T);
-    const Rep r = load_rep(sm.ctl);
+    const Rep r = load_rep(sm.ctl->rep);
     uint32_t f = 0;
     Pow pw = {0u, 0u};
-    if (!STATS) f = phase_replace<BITS, RMODE, T, PW>(sm, w, r, p, tid, par, pw);
-    if (!STATS && RMODE == 3) {
+    const KeysPre key{p};
+    if (!STATS && !COPIES) f = phase_replace<BITS, RMODE, T, PW>(sm, w, r, key, tid, &sm.ctl->ncount[par], pw, &sm.ctl->rep);
+    if (!STATS && !COPIES && RMODE == 3) {
         if (BITS == 8) {
-            noise_deferred8<T, PW>(sm, w, r, p, tid, f, pw);
+            noise_deferred8<T, PW>(sm, w, r, key, tid, f, pw);
         } else {
             named_bar(sm.bar_id, T);  // every flagged position of the window is in the list
-            noise_list<BITS, T, PW>(sm, w, r, p, tid, par, pw);
+            noise_list<BITS, T, PW>(sm, w, r, key, tid, &sm.ctl->ncount[par], pw);
+        }
+    }
+    if (COPIES) {
+        // every variant's values from the window's M and D, then its replace pass
+        if (tid < params_nvar(p)) {
+            const Variant vr = params_var(p)[tid];
+            sm.cp->vrep[tid] = make_rep<BITS>(r.M, r.D, vr.kq, vr.cval);
+        }
+        named_bar(sm.bar_id, T);
+        for (int v = 0; v < params_nvar(p); ++v) {
+            const Variant vr = params_var(p)[v];
+            const Seg &sv = vsegs[static_cast<int64_t>(v) * params_seg_stride(p)];
+            Win wv = w;
+            wv.out = sv.out + widx * sv.W * Geo<BITS>::kBps;
+            wv.mask = sv.mask ? sv.mask + widx * sv.mask_words : nullptr;
+            wv.vec = sv.vec != 0;
+            const Rep rv = load_rep(sm.cp->vrep[v]);
+            const KeysSeed vkey{static_cast<uint32_t>(vr.seed), static_cast<uint32_t>(vr.seed >> 32)};
+            uint32_t *nc = &sm.cp->ncount[2 * v + par];
+            uint32_t fv;
+            switch (vr.mode) {
+                case 0: fv = phase_replace<BITS, 0, T, false>(sm, wv, rv, vkey, tid, nc, pw, &sm.cp->vrep[v]); break;
+                case 1: fv = phase_replace<BITS, 1, T, false>(sm, wv, rv, vkey, tid, nc, pw, &sm.cp->vrep[v]); break;
+                case 2: fv = phase_replace<BITS, 2, T, false>(sm, wv, rv, vkey, tid, nc, pw, &sm.cp->vrep[v]); break;
+                default:
+                    fv = phase_replace<BITS, 3, T, false>(sm, wv, rv, vkey, tid, nc, pw, &sm.cp->vrep[v]);
+                    if (BITS == 8) {
+                        noise_deferred8<T, false>(sm, wv, rv, vkey, tid, fv, pw);
+                    } else {
+                        named_bar(sm.bar_id, T);
+                        noise_list<BITS, T, false>(sm, wv, rv, vkey, tid, nc, pw);
+                    }
+                    // the noise work area and the first indices are reused by the next variant
+                    if (v + 1 < params_nvar(p)) named_bar(sm.bar_id, T);
+                    break;
+            }
+            fv = __reduce_add_sync(0xFFFFFFFFu, fv);
+            if (lane == 0 && fv) atomicAdd(&sm.cp->vcount[v][par], fv);
         }
     }
     f = __reduce_add_sync(0xFFFFFFFFu, f);
@@ -964,6 +1031,15 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
             const uint32_t cnt = atomicExch(&sm.ctl->count[par], 0u);
             sm.ctl->done[par] = 0u;
             if (BITS == 12 && RMODE == 3) sm.ctl->ncount[par] = 0u;  // every warp has read it
+            if (COPIES) {
+                for (int v = 0; v < params_nvar(p); ++v) {
+                    const uint32_t cv = atomicExch(&sm.cp->vcount[v][par], 0u);
+                    sm.cp->ncount[2 * v + par] = 0u;
+                    const Seg &sv = vsegs[static_cast<int64_t>(v) * params_seg_stride(p)];
+                    if (sv.counts) sv.counts[widx] = cv;
+                    sm.ctl->flagged += cv;
+                }
+            }
             if (PW) {
                 const unsigned long long sx = atomicExch(&sm.ctl->pw[par][0], 0ull);
                 const unsigned long long sz = atomicExch(&sm.ctl->pw[par][1], 0ull);
@@ -972,7 +1048,7 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
                     sg.power[2 * widx + 1] = sz;
                 }
             }
-            if (sg.counts) sg.counts[widx] = cnt;
+            if (!COPIES && sg.counts) sg.counts[widx] = cnt;
             if (!APPLY && sg.med) sg.med[widx] = r.M;
             if (!APPLY && sg.mad) sg.mad[widx] = r.D;
             sm.ctl->flagged += cnt;

@@ -21,6 +21,19 @@ constexpr int kApplyTileWindows = 32;  // at most this many windows per tile in 
 // (the detected power of the unfiltered and filtered signal, for the improvement metric of
 // Section III-A) and writes them to Seg::power.
 constexpr int kModePower = 16;
+// Flag bit of the digital-copy pass (Section III-A): one histogram, median and MAD per window and
+// up to kMaxCopies (k, replacement) variants written to their own outputs. The variants come
+// from Params::var; variant v of segment s is segment v * Params::seg_stride + s.
+constexpr int kModeCopies = 32;
+constexpr int kMaxCopies = 8;
+
+// One variant of a digital-copy pass.
+struct Variant {
+    int64_t kq;     // round(k * 1.4826 * 2^16)
+    uint64_t seed;  // noise key
+    int32_t cval;   // constant replacement, already saturated
+    int32_t mode;   // rfi_mode
+};
 
 // Device counters of one kernel pass, reset before it.
 struct DevCounters {
@@ -64,7 +77,19 @@ struct Params {
     uint32_t *status;             // device status word (atomicOr of kStatus*)
     unsigned long long *flagged;  // device total of flagged samples
     uint32_t rk0[10], rk1[10];    // Philox4x32-10 round keys of `seed` (see set_round_keys)
+    // Digital copy: the number of variants (bits 0-3) and the distance between one variant's
+    // segment table and the next (bits 4-31), and the byte offset of the variant table from the
+    // status word (both live in the plan's workspace). Packed into 8 bytes: a larger parameter
+    // block changes the register allocation of every excision kernel for the worse.
+    int32_t copies;
+    int32_t var_off;
 };
+
+__host__ __device__ inline int params_nvar(const Params &p) { return p.copies & 15; }
+__host__ __device__ inline int params_seg_stride(const Params &p) { return p.copies >> 4; }
+__host__ __device__ inline const Variant *params_var(const Params &p) {
+    return reinterpret_cast<const Variant *>(reinterpret_cast<const char *>(p.status) + p.var_off);
+}
 
 // Philox4x32-10 key schedule: round r uses (seed_lo + r * 0x9E3779B9, seed_hi + r * 0xBB67AE85)
 // (the Weyl increments of Salmon et al., SC'11), precomputed so kernels read them as constants.

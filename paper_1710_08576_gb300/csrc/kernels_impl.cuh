@@ -33,6 +33,7 @@ struct Layout {
     int cum, ctl, bar, meta;  // offsets inside a group block
     int nlist;                // digital-noise position list inside a group block (0: none)
     int amd;                  // apply passes: per stage, {M, dispersion} of its windows (0: none)
+    int cps;                  // digital copy: per-variant state inside a group block (0: none)
     int stage;      // first stage buffer; group g stage s at stage + (g * stages + s) * stage_bytes
     int total;
 };
@@ -46,12 +47,15 @@ __host__ __device__ inline Layout layout(int ncopies, int stages, int stage_byte
     L.bar = align_up(L.ctl + static_cast<int>(sizeof(Ctl)), 128);
     L.meta = align_up(L.bar + (2 * kMaxStages + 1) * 8, 128);
     const int meta_end = align_up(L.meta + kMaxStages * static_cast<int>(sizeof(StageMeta)), 128);
-    const bool noise = (mode & 3) == 3 && (mode & kModeStats) == 0;
+    const bool noise = ((mode & 3) == 3 || (mode & kModeCopies) != 0) && (mode & kModeStats) == 0;
     L.nlist = noise ? meta_end : 0;
     const int list_end = noise ? align_up(meta_end + kNoiseList * 2, 128) : meta_end;
     const bool apply = (mode & kModeApply) != 0;
     L.amd = apply ? list_end : 0;
-    L.grp_size = apply ? align_up(list_end + kMaxStages * kApplyTileWindows * 8, 128) : list_end;
+    const int amd_end = apply ? align_up(list_end + kMaxStages * kApplyTileWindows * 8, 128) : list_end;
+    const bool copies = (mode & kModeCopies) != 0;
+    L.cps = copies ? amd_end : 0;
+    L.grp_size = copies ? align_up(amd_end + static_cast<int>(sizeof(CopyShared)), 128) : amd_end;
     L.stage = L.grp + groups * L.grp_size;
     L.total = L.stage + groups * stages * stage_bytes;
     return L;
@@ -70,6 +74,7 @@ __device__ __forceinline__ Shm group_view(uint8_t *smem, const Layout &L, int g,
     sm.ncopies = ncopies;
     sm.bar_id = 1 + g;
     sm.nlist = L.nlist ? reinterpret_cast<uint16_t *>(gb + L.nlist) : nullptr;
+    sm.cp = L.cps ? reinterpret_cast<CopyShared *>(gb + L.cps) : nullptr;
     return sm;
 }
 
@@ -240,7 +245,8 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
                                   ? reinterpret_cast<const int2 *>(gb + L.amd) + s * kApplyTileWindows + k
                                   : nullptr;
             alive = process_window<BITS, MODE, T, Geo<BITS>::row_bytes(G)>(
-                sm, win, sg, widx, p, tid, par, k + 1 == tl.nw ? empty_bar(s) : 0u, true, rs, amd);
+                sm, win, sg, widx, p, tid, par, k + 1 == tl.nw ? empty_bar(s) : 0u, true, rs, amd,
+                (MODE & kModeCopies) ? segs + tl.seg : nullptr);
             par ^= 1;
         }
         if (!alive) {

@@ -214,7 +214,7 @@ extern "C" rfi_status rfi_excise_noalloc(const rfi_plan_desc *d, const void *con
     write_tiles_kernel<<<(ntiles + 255) / 256, 256, 0, st>>>(tiles, spec);
     if (cudaGetLastError() != cudaSuccess) return RFI_ERR_CUDA;
 
-    Params p;
+    Params p{};
     p.kq = kq;
     p.seed = d->seed;
     const int32_t lo = bps == 1 ? -128 : -2048, hi = bps == 1 ? 127 : 2047;

@@ -1,7 +1,8 @@
 // The passes beyond plain excision: for the Median of MAD (Eq. 3), the sliding lower median of
 // the last k_mom per-window MADs of each stream and the estimation-only / apply instantiations
-// of the persistent kernel around it; and the power-metered excision (per-window sums of x^2
-// and z^2 for the improvement metric of Section III-A). Instantiated per sample width in
+// of the persistent kernel around it; the power-metered excision (per-window sums of x^2 and
+// z^2 for the improvement metric of Section III-A); and the digital-copy pass (several (k,
+// replacement) variants from one histogram per window). Instantiated per sample width in
 // passes8.cu / passes12.cu.
 #pragma once
 
@@ -117,6 +118,7 @@ cudaError_t mom_launch_t(const MomChunk *chunks, int nchunks, const int32_t *D, 
             RFI_CASES_MOM_CW(BITS, FN, 17, __VA_ARGS__)                 \
             RFI_CASES_MOM_CW(BITS, FN, 18, __VA_ARGS__)                 \
             RFI_CASES_MOM_CW(BITS, FN, 19, __VA_ARGS__)                 \
+            RFI_CASES_MOM_CW(BITS, FN, 32, __VA_ARGS__)                 \
             default: break;                                             \
         }                                                               \
     } while (0)

@@ -53,7 +53,7 @@ rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req) {
     const int min_stage = static_cast<int>((maxwb + 127) / 128 * 128);
     s.consumer_warps = (req && req->consumer_warps) ? req->consumer_warps : 8;
     s.groups = (req && req->groups) ? req->groups : 1;
-    if (P->kmom >= 2 || P->power) {  // these passes are built for one group of 4 or 8 consumer warps
+    if (P->kmom >= 2 || P->power || P->ncopy > 0) {  // built for one group of 4 or 8 consumer warps
         if ((req && req->groups > 1) || s.consumer_warps > 8) return RFI_ERR_UNSUPPORTED;
         s.groups = 1;
     }
@@ -129,7 +129,8 @@ rfi_status plan_alloc_workspace(rfi_plan_s *P) {
     }
     const size_t mc_b = mom ? al(sizeof(MomChunk) * P->mchunks.size()) : 0;
     const size_t pw_b = P->power ? al(2 * sizeof(uint64_t) * P->total_windows) : 0;
-    P->ws_bytes = seg_b + tile_b + (mom ? 3 : 2) * md_b + mc_b + pw_b + ctr_b;
+    const size_t var_b = al(sizeof(Variant) * P->variants.size());
+    P->ws_bytes = seg_b + tile_b + (mom ? 3 : 2) * md_b + mc_b + pw_b + var_b + ctr_b;
     if (P->ws) cudaFree(P->ws);
     P->ws = nullptr;
     if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
@@ -153,12 +154,17 @@ rfi_status plan_alloc_workspace(rfi_plan_s *P) {
                             cudaMemcpyHostToDevice));
     }
     if (P->power) P->d_pow = reinterpret_cast<uint64_t *>(b + ctr_b + seg_b + tile_b + 2 * md_b + mc_b);
+    if (!P->variants.empty()) {
+        P->d_var = reinterpret_cast<Variant *>(b + ctr_b + seg_b + tile_b + (mom ? 3 : 2) * md_b + mc_b + pw_b);
+        RFI_CUDA(cudaMemcpy(P->d_var, P->variants.data(), sizeof(Variant) * P->variants.size(),
+                            cudaMemcpyHostToDevice));
+    }
     P->segs_valid = false;
     return RFI_OK;
 }
 
 Params plan_params(const rfi_plan_s *P) {
-    Params p;
+    Params p{};
     p.kq = P->kq;
     p.seed = P->seed;
     p.cval = P->cval;
@@ -166,6 +172,10 @@ Params plan_params(const rfi_plan_s *P) {
     p.status = &P->d_ctr->status;
     p.flagged = &P->d_ctr->flagged;
     set_round_keys(p);
+    p.copies = P->ncopy | (P->S << 4);
+    p.var_off = P->d_var ? static_cast<int32_t>(reinterpret_cast<const char *>(P->d_var) -
+                                                reinterpret_cast<const char *>(&P->d_ctr->status))
+                         : 0;
     return p;
 }
 
@@ -284,9 +294,27 @@ const char *rfi_status_string(rfi_status s) {
     return "unknown status";
 }
 
-rfi_status rfi_plan_create(const rfi_plan_desc *d, rfi_plan_t *out_plan) {
+static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_variant *vars, rfi_plan_t *out_plan);
+
+rfi_status rfi_plan_create(const rfi_plan_desc *d, rfi_plan_t *out_plan) { return plan_create(d, 0, nullptr, out_plan); }
+
+rfi_status rfi_plan_create_copies(const rfi_plan_desc *d, int32_t nvariants, const rfi_variant *variants,
+                                  rfi_plan_t *out_plan) {
+    if (!d || !out_plan || !variants || nvariants < 1 || nvariants > kMaxCopies) return RFI_ERR_INVALID_ARG;
+    return plan_create(d, nvariants, variants, out_plan);
+}
+
+static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_variant *vars, rfi_plan_t *out_plan) {
     if (!d || !out_plan) return RFI_ERR_INVALID_ARG;
     *out_plan = nullptr;
+    if (nvar > 0) {
+        for (int v = 0; v < nvar; ++v) {
+            if (!(vars[v].k > 0.0) || !std::isfinite(vars[v].k) || vars[v].k > 1.0e6) return RFI_ERR_INVALID_ARG;
+            if (vars[v].mode < RFI_REPLACE_ZERO || vars[v].mode > RFI_REPLACE_NOISE) return RFI_ERR_INVALID_ARG;
+            if (static_cast<int64_t>(std::floor(vars[v].k * 1.4826 * 65536.0 + 0.5)) < 1) return RFI_ERR_INVALID_ARG;
+        }
+        if ((d->flags & (RFI_PLAN_PER_STREAM | RFI_PLAN_POWER)) || d->mom_windows >= 2) return RFI_ERR_UNSUPPORTED;
+    }
     if (d->sample_bits != 8 && d->sample_bits != 12) return RFI_ERR_INVALID_ARG;
     if (d->num_streams < 1 || !d->stream_len || !d->window_len) return RFI_ERR_INVALID_ARG;
     if (!(d->k > 0.0) || !std::isfinite(d->k) || d->k > 1.0e6) return RFI_ERR_INVALID_ARG;
@@ -327,6 +355,15 @@ rfi_status rfi_plan_create(const rfi_plan_desc *d, rfi_plan_t *out_plan) {
     P->seed = d->seed;
     P->kmom = d->mom_windows >= 2 ? d->mom_windows : 0;
     P->power = (d->flags & RFI_PLAN_POWER) != 0;
+    P->ncopy = nvar;
+    for (int v = 0; v < nvar; ++v) {
+        Variant vr;
+        vr.kq = static_cast<int64_t>(std::floor(vars[v].k * 1.4826 * 65536.0 + 0.5));
+        vr.seed = vars[v].seed;
+        vr.cval = std::min(hi, std::max(lo, vars[v].const_value));
+        vr.mode = vars[v].mode;
+        P->variants.push_back(vr);
+    }
     P->len.assign(d->stream_len, d->stream_len + P->S);
     P->W.assign(d->window_len, d->window_len + P->S);
     P->sid.resize(P->S);
@@ -350,7 +387,7 @@ rfi_status rfi_plan_create(const rfi_plan_desc *d, rfi_plan_t *out_plan) {
         return RFI_ERR_CUDA;
     }
     // windows of very different sizes: one internal plan per stage class
-    if (!(P->flags & (RFI_PLAN_PER_STREAM | RFI_PLAN_NO_SPLIT))) {
+    if (!(P->flags & (RFI_PLAN_PER_STREAM | RFI_PLAN_NO_SPLIT)) && P->ncopy == 0) {
         const int bps = P->bits == 8 ? 1 : 2;
         std::vector<std::vector<int>> cls(3);
         for (int i = 0; i < P->S; ++i)
@@ -391,7 +428,7 @@ rfi_status rfi_plan_create(const rfi_plan_desc *d, rfi_plan_t *out_plan) {
     if (rs == RFI_OK) rs = plan_build_tiles(P);
     if (rs == RFI_OK) rs = plan_alloc_workspace(P);
     if (rs == RFI_OK && (P->flags & RFI_PLAN_AUTOTUNE) && !(P->flags & RFI_PLAN_PER_STREAM) && P->kmom < 2 &&
-        !P->power)
+        !P->power && P->ncopy == 0)
         rs = plan_autotune(P, d->shape);
     if (rs == RFI_OK && (P->flags & RFI_PLAN_GRAPH)) rs = plan_build_graph(P);
     if (rs != RFI_OK) {
@@ -419,6 +456,7 @@ rfi_status rfi_excise(rfi_plan_t P, const void *const *in, void *const *out, uin
         P->last_windows = P->total_windows;
         return RFI_OK;
     }
+    if (P->ncopy > 0) return RFI_ERR_INVALID_ARG;  // digital-copy plans take rfi_excise_copies
     rfi_status rs = plan_check_buffers(P, in, out, mask, counts);
     if (rs != RFI_OK) return rs;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -431,6 +469,32 @@ rfi_status rfi_excise(rfi_plan_t P, const void *const *in, void *const *out, uin
             RFI_CUDA(launch_stream(P->bits, P->mode, P->shape.consumer_warps, segs[i], 0, P->nwin[i], p, st));
         return RFI_OK;
     }
+    return plan_run_batched(P, segs, st);
+}
+
+rfi_status rfi_excise_copies(rfi_plan_t P, const void *const *in, void *const *out, uint32_t *const *mask,
+                             uint32_t *const *counts, void *stream) {
+    if (!P || P->ncopy < 1 || !in || !out) return RFI_ERR_INVALID_ARG;
+    std::vector<Seg> segs;
+    for (int v = 0; v < P->ncopy; ++v) {
+        void *const *o = out + static_cast<size_t>(v) * P->S;
+        uint32_t *const *m = mask ? mask + static_cast<size_t>(v) * P->S : nullptr;
+        uint32_t *const *c = counts ? counts + static_cast<size_t>(v) * P->S : nullptr;
+        rfi_status rs = plan_check_buffers(P, in, o, m, c);
+        if (rs != RFI_OK) return rs;
+        const std::vector<Seg> sv = plan_segs(P, in, o, m, c);
+        segs.insert(segs.end(), sv.begin(), sv.begin() + P->S);
+    }
+    P->last_windows = P->total_windows;
+    return plan_run_batched(P, segs, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace rfi {
+
+// Refresh the device segment table if the buffers changed, then run the batched pass.
+rfi_status plan_run_batched(rfi_plan_s *P, const std::vector<Seg> &segs, cudaStream_t st) {
     const int nsegs = plan_nsegs(P);
     if (!P->segs_valid || std::memcmp(segs.data(), P->segs_host.data(), sizeof(Seg) * nsegs) != 0) {
         for (int i = 0; i < nsegs; i += kSegBatch)
@@ -447,6 +511,10 @@ rfi_status rfi_excise(rfi_plan_t P, const void *const *in, void *const *out, uin
     }
     return plan_enqueue_batched(P, st);
 }
+
+}  // namespace rfi
+
+extern "C" {
 
 rfi_status rfi_stats(rfi_plan_t P, int32_t *const *median, int32_t *const *mad, rfi_totals *totals, void *stream) {
     if (!P) return RFI_ERR_INVALID_ARG;

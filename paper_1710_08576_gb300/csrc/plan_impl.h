@@ -56,6 +56,10 @@ struct rfi_plan_s {
     // RFI_PLAN_POWER: {sum x^2, sum z^2} per window
     bool power = false;
     uint64_t *d_pow = nullptr;
+    // digital copy: the variants (segment table holds ncopy * S entries)
+    int ncopy = 0;
+    std::vector<rfi::Variant> variants;
+    rfi::Variant *d_var = nullptr;
     rfi::MomChunk *d_mchunks = nullptr;
     std::vector<rfi::MomChunk> mchunks;
     std::vector<rfi::Seg> segs_host;
@@ -84,7 +88,10 @@ std::vector<Seg> plan_segs(const rfi_plan_s *P, const void *const *in, void *con
                            uint32_t *const *counts);
 rfi_status plan_check_buffers(const rfi_plan_s *P, const void *const *in, void *const *out,
                               uint32_t *const *mask, uint32_t *const *counts);
-inline int plan_nsegs(const rfi_plan_s *P) { return P->kmom >= 2 ? 2 * P->S : P->S; }
+rfi_status plan_run_batched(rfi_plan_s *P, const std::vector<Seg> &segs, cudaStream_t st);
+inline int plan_nsegs(const rfi_plan_s *P) {
+    return P->kmom >= 2 ? 2 * P->S : (P->ncopy > 0 ? P->ncopy * P->S : P->S);
+}
 // Stage class of a window of wb bytes: 0 up to 16 KiB, 1 up to 32 KiB, 2 larger.
 inline int window_class(int64_t wb) { return wb <= 16384 ? 0 : (wb <= 32768 ? 1 : 2); }
 // Per-part pointer arrays of a split plan (entries in the part's stream order).
@@ -95,6 +102,8 @@ std::vector<T> part_args(const rfi_plan_s *P, size_t k, T const *all) {
     return v;
 }
 // Kernel mode of a per-window MAD plan (the power-metered form when RFI_PLAN_POWER is set).
-inline int plan_kernel_mode(const rfi_plan_s *P) { return P->mode | (P->power ? kModePower : 0); }
+inline int plan_kernel_mode(const rfi_plan_s *P) {
+    return P->ncopy > 0 ? kModeCopies : (P->mode | (P->power ? kModePower : 0));
+}
 
 }  // namespace rfi

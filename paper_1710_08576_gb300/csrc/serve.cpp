@@ -182,7 +182,7 @@ namespace {
     } while (0)
 
 Params server_params(const rfi_server_s *s, DevCounters *ctr) {  // ctr: the server's counters
-    Params p;
+    Params p{};
     p.kq = s->kq;
     p.seed = s->seed;
     p.cval = s->cval;
