@@ -84,6 +84,10 @@ typedef enum rfi_mode {
 } rfi_mode;
 
 /* rfi_plan_desc.flags */
+/* Output sample type (Section II-C: the excised stream feeds the correlator and beamformer,
+ * whose channeliser FFT reads real values): the input's own type, or fp16 / bf16. */
+typedef enum { RFI_OUT_SAME = 0, RFI_OUT_F16 = 1, RFI_OUT_BF16 = 2 } rfi_out_format;
+
 #define RFI_PLAN_PER_STREAM 0x1u  /* one launch per stream, one CTA per window */
 #define RFI_PLAN_BATCHED 0x2u     /* one persistent launch over all windows (default) */
 #define RFI_PLAN_GRAPH 0x4u       /* batched launch replayed from a CUDA graph */
@@ -130,6 +134,13 @@ typedef struct rfi_plan_desc {
                                      and rfi_excise_host return RFI_ERR_UNSUPPORTED; the launch
                                      shape is fixed (one group of 4 or 8 consumer warps) and
                                      RFI_PLAN_AUTOTUNE has no effect. */
+    int32_t out_format;           /* rfi_out_format: the type of the excised samples written to
+                                     out (2 bytes per sample for fp16 / bf16); the samples'
+                                     values are exact in both. fp16 and bf16 need the batched
+                                     form (RFI_ERR_UNSUPPORTED with RFI_PLAN_PER_STREAM,
+                                     rfi_excise_host, mom_windows >= 2, RFI_PLAN_POWER, and bf16
+                                     with 12-bit samples); out must be 2-byte aligned; fixed
+                                     launch shape. */
 } rfi_plan_desc;
 
 typedef struct rfi_plan_s *rfi_plan_t;

@@ -30,6 +30,7 @@ RFI_PLAN_GRAPH = 0x4
 RFI_PLAN_AUTOTUNE = 0x8
 RFI_PLAN_POWER = 0x10
 RFI_PLAN_NO_SPLIT = 0x20
+RFI_OUT_SAME, RFI_OUT_F16, RFI_OUT_BF16 = 0, 1, 2
 RFI_PLAN_INJECT_TIMEOUT = 0x100
 
 
@@ -47,7 +48,7 @@ class RfiPlanDesc(ctypes.Structure):
                 ("stream_id", ctypes.POINTER(ctypes.c_uint32)), ("k", ctypes.c_double),
                 ("mode", ctypes.c_int32), ("const_value", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("flags", ctypes.c_uint32), ("shape", ctypes.POINTER(RfiLaunchShape)),
-                ("mom_windows", ctypes.c_int32)]
+                ("mom_windows", ctypes.c_int32), ("out_format", ctypes.c_int32)]
 
 
 class RfiVariant(ctypes.Structure):
@@ -192,7 +193,7 @@ def _stream(stream) -> int:
 
 
 def make_desc(bits, stream_len, window_len, k, mode, const_value=0, seed=0, flags=0, stream_id=None,
-              shape=None, mom_windows=0):
+              shape=None, mom_windows=0, out_format=0):
     n = len(stream_len)
     keep = []
     lens = (ctypes.c_int64 * n)(*[int(v) for v in stream_len])
@@ -209,7 +210,7 @@ def make_desc(bits, stream_len, window_len, k, mode, const_value=0, seed=0, flag
         shp = ctypes.pointer(shape)
         keep.append(shape)
     d = RfiPlanDesc(int(bits), n, lens, wins, sid, float(k), int(mode), int(const_value), int(seed),
-                    int(flags), shp, int(mom_windows))
+                    int(flags), shp, int(mom_windows), int(out_format))
     d._keep = keep
     return d
 
@@ -375,9 +376,9 @@ class Plan:
     """Owns one rfi_plan_t. Buffers are torch tensors (or raw device pointers)."""
 
     def __init__(self, bits, stream_len, window_len, k, mode, const_value=0, seed=0, flags=0,
-                 stream_id=None, shape=None, mom_windows=0):
+                 stream_id=None, shape=None, mom_windows=0, out_format=0):
         self.desc = make_desc(bits, stream_len, window_len, k, mode, const_value, seed, flags,
-                              stream_id, shape, mom_windows)
+                              stream_id, shape, mom_windows, out_format)
         st, h = rfi_plan_create(self.desc)
         check(st, "rfi_plan_create")
         self.handle = h

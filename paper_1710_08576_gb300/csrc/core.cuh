@@ -38,6 +38,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -625,6 +627,69 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int j) {
     return pos + ((j >= static_cast<int>(m & 1u)) ? 1 : 0);
 }
 
+// ------------------------------------------------------------------ output formats
+// OUTF 0 writes the input's type; 1 writes fp16 and 2 bf16 (int8 input only). Every sample value
+// is exact in either: |x| <= 2048 needs 12 significant bits (fp16 has 11 + 1) and int8 needs 8
+// (bf16 has 7 + 1).
+template <int BITS, int OUTF>
+__device__ __forceinline__ void store_sample(uint8_t *out, int pos, int32_t z) {
+    if (OUTF == 1) reinterpret_cast<__half *>(out)[pos] = __int2half_rn(z);
+    else if (OUTF == 2) reinterpret_cast<__nv_bfloat16 *>(out)[pos] = __int2bfloat16_rn(z);
+    else if (BITS == 8) out[pos] = static_cast<uint8_t>(z);
+    else reinterpret_cast<int16_t *>(out)[pos] = static_cast<int16_t>(z);
+}
+
+// The 16 int8 output samples of chunk c (v holds them as bytes) in format OUTF: 16-byte stores
+// when vec, else one sample at a time. fp16: a biased byte u = x + 128 placed under 0x64 is the
+// fp16 1024 + u, and subtracting 1152 leaves x. bf16: u placed in the fp32 2^23 + u, minus
+// 2^23 + 128, leaves x as fp32; its bf16 rounding is exact.
+template <int OUTF>
+__device__ __forceinline__ void store_chunk8(uint8_t *out, int c, const uint4 &v, bool vec) {
+    const uint32_t ww[4] = {v.x, v.y, v.z, v.w};
+    if constexpr (OUTF == 0) {
+        if (vec) {
+            __stcs(reinterpret_cast<uint4 *>(out) + c, v);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) out[c * 16 + j] = static_cast<uint8_t>(ww[j >> 2] >> ((j & 3) * 8));
+        }
+    } else {
+        uint32_t h[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t u = ww[q] ^ 0x80808080u;
+            if (OUTF == 1) {
+                const __half2 off = __half2half2(__ushort_as_half(static_cast<unsigned short>(0x6480u)));  // 1152
+                __half2 lo, hi;
+                *reinterpret_cast<uint32_t *>(&lo) = __byte_perm(u, 0x64646464u, 0x5140u);
+                *reinterpret_cast<uint32_t *>(&hi) = __byte_perm(u, 0x64646464u, 0x7362u);
+                lo = __hsub2(lo, off);
+                hi = __hsub2(hi, off);
+                h[2 * q] = *reinterpret_cast<uint32_t *>(&lo);
+                h[2 * q + 1] = *reinterpret_cast<uint32_t *>(&hi);
+            } else {
+                float f[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    f[k] = __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7540u | k)) - 8388736.0f;
+                const __nv_bfloat162 a = __floats2bfloat162_rn(f[0], f[1]);
+                const __nv_bfloat162 b = __floats2bfloat162_rn(f[2], f[3]);
+                h[2 * q] = *reinterpret_cast<const uint32_t *>(&a);
+                h[2 * q + 1] = *reinterpret_cast<const uint32_t *>(&b);
+            }
+        }
+        if (vec) {
+            uint4 *o = reinterpret_cast<uint4 *>(out) + 2 * c;
+            __stcs(o, make_uint4(h[0], h[1], h[2], h[3]));
+            __stcs(o + 1, make_uint4(h[4], h[5], h[6], h[7]));
+        } else {
+            uint16_t *o = reinterpret_cast<uint16_t *>(out) + 16 * c;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) o[j] = static_cast<uint16_t>(h[j >> 1] >> ((j & 1) * 16));
+        }
+    }
+}
+
 // Digital noise for the flagged samples of up to four rounds of the warp. Lane l holds in nb
 // the 16-bit flag masks of its chunks c0 + k*T (k = 0..3, mask k in bits [16k, 16k+16)). The
 // flagged samples are numbered across the warp (an exclusive prefix sum of the per-lane
@@ -632,7 +697,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int j) {
 // that owns it and a popcount search for its bit, and all 32 lanes evaluate Philox together.
 // The stores go straight to the output; they follow the chunks' own stores in warp order
 // (__syncwarp before the call).
-template <int BITS, int T, bool PW, class K>
+template <int BITS, int T, bool PW, class K, int OUTF = 0>
 __device__ __forceinline__ void noise_batch(const Win &w, const Rep &r, const K &p, int lane, int c0,
                                             uint64_t nb, Pow &pw) {
     constexpr int CS = Geo<BITS>::kChunkSamples;
@@ -667,8 +732,7 @@ __device__ __forceinline__ void noise_batch(const Win &w, const Rep &r, const K 
             const int bp = (inlo ? 0 : 32) + nth_set_bit(inlo ? loL : hiL, inlo ? j : j - clo);
             const int pos = (cL + (bp >> 4) * T) * CS + (bp & 15);
             const int32_t z = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pos, Geo<BITS>::kLo, Geo<BITS>::kHi);
-            if (BITS == 8) w.out[pos] = static_cast<uint8_t>(z);
-            else reinterpret_cast<int16_t *>(w.out)[pos] = static_cast<int16_t>(z);
+            store_sample<BITS, OUTF>(w.out, pos, z);
             if (PW) pw.z += static_cast<uint32_t>(z * z);
         }
     }
@@ -679,7 +743,7 @@ __device__ __forceinline__ void noise_batch(const Win &w, const Rep &r, const K 
 // 65536 samples (position 65535 would equal the skip mark) and rounds that do not fit in the
 // list take the per-warp path at once; list entries reserved beyond the written ones are
 // marked skipped. Called by all lanes of the warp with the round's chunk c and flag bits.
-template <int BITS, int T, bool PW, class K>
+template <int BITS, int T, bool PW, class K, int OUTF = 0>
 __device__ __forceinline__ void noise_append(const Shm &sm, const Win &w, const Rep &r, const K &p, int lane,
                                              int c, uint32_t bits, uint32_t *nlc, Pow &pw) {
     constexpr int CS = Geo<BITS>::kChunkSamples;
@@ -703,12 +767,12 @@ __device__ __forceinline__ void noise_append(const Shm &sm, const Win &w, const 
     }
     for (uint32_t i = base + lane; i < static_cast<uint32_t>(kNoiseList); i += 32) sm.nlist[i] = kNoiseSkip;
     __syncwarp();  // the round's chunk stores come first
-    noise_batch<BITS, T, PW, K>(w, r, p, lane, c, static_cast<uint64_t>(bits), pw);
+    noise_batch<BITS, T, PW, K, OUTF>(w, r, p, lane, c, static_cast<uint64_t>(bits), pw);
 }
 
 // Digital noise, after the group barrier that follows the replace pass: every thread of the
 // group evaluates Philox for a share of the list and stores the value over the chunk's output.
-template <int BITS, int T, bool PW, class K>
+template <int BITS, int T, bool PW, class K, int OUTF = 0>
 __device__ __forceinline__ void noise_list(const Shm &sm, const Win &w, const Rep &r, const K &p, int tid,
                                            uint32_t *nlc, Pow &pw) {
     if (sm.nlist == nullptr) return;
@@ -717,8 +781,7 @@ __device__ __forceinline__ void noise_list(const Shm &sm, const Win &w, const Re
         const uint32_t pos = sm.nlist[i];
         if (pos == kNoiseSkip) continue;
         const int32_t z = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pos, Geo<BITS>::kLo, Geo<BITS>::kHi);
-        if (BITS == 8) w.out[pos] = static_cast<uint8_t>(z);
-        else reinterpret_cast<int16_t *>(w.out)[pos] = static_cast<int16_t>(z);
+        store_sample<BITS, OUTF>(w.out, pos, z);
         if (PW) pw.z += static_cast<uint32_t>(z * z);
     }
 }
@@ -731,7 +794,7 @@ __device__ __forceinline__ void noise_list(const Shm &sm, const Win &w, const Re
 // flagged sample starts below 65536), walks the owner's chunks to the sample and evaluates
 // Philox for it. Every walk is bounded by the window and every store is checked against the
 // window's length.
-template <int T, bool PW, class K>
+template <int T, bool PW, class K, int OUTF = 0>
 __device__ __forceinline__ void noise_deferred8(const Shm &sm, const Win &w, const Rep &r, const K &p, int tid,
                                                 uint32_t cnt, Pow &pw) {
     constexpr int NW = T / 32;
@@ -760,7 +823,7 @@ __device__ __forceinline__ void noise_deferred8(const Shm &sm, const Win &w, con
         const int pos = c * 16 + nth_set_bit(b, static_cast<int>(j));
         if (pos >= w.n) continue;
         const int32_t z = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pos, Geo<8>::kLo, Geo<8>::kHi);
-        w.out[pos] = static_cast<uint8_t>(z);
+        store_sample<8, OUTF>(w.out, pos, z);
         if (PW) pw.z += static_cast<uint32_t>(z * z);
     }
 }
@@ -772,7 +835,7 @@ __device__ __forceinline__ uint32_t sq4(uint32_t w, uint32_t keep) {
 }
 
 // rsrc: the shared record r was loaded from (its int8 constants are read from there).
-template <int BITS, int MODE, int T, bool PW, class K>
+template <int BITS, int MODE, int T, bool PW, class K, int OUTF = 0>
 __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, const Rep &r, const K &p,
                                                   int tid, uint32_t *nlc, Pow &pw, const RepShared *rsrc) {
     constexpr int BPS = Geo<BITS>::kBps;
@@ -796,7 +859,6 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
         k.usmall = q3.w;
         k.unone = q4.x;
         uint16_t *mk = reinterpret_cast<uint16_t *>(w.mask);
-        uint4 *o4 = reinterpret_cast<uint4 *>(w.out);
         int base = warp * 32;
         if (r.active && w.vec && mk) {
             // rounds in which all 32 chunks of the warp are full: no bounds checks
@@ -810,7 +872,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 v.z = rep8_word<MODE>(v.z, k, f2);
                 v.w = rep8_word<MODE>(v.w, k, f3);
                 const uint32_t bits = chunk_bits(f0, f1, f2, f3);
-                __stcs(o4 + c, v);
+                store_chunk8<OUTF>(w.out, c, v, true);
                 if (PW) pw.z += sq4(v.x, ~0u) + sq4(v.y, ~0u) + sq4(v.z, ~0u) + sq4(v.w, ~0u);
                 mk[c] = static_cast<uint16_t>(bits);
                 flagged += __popc(bits);
@@ -833,19 +895,14 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                     bits = chunk_bits(f0, f1, f2, f3);
                 }
                 if (c < nfull) {
-                    if (w.vec) __stcs(o4 + c, v);
-                    else {
-                        const uint32_t ww[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) w.out[c * 16 + j] = static_cast<uint8_t>(ww[j >> 2] >> ((j & 3) * 8));
-                    }
+                    store_chunk8<OUTF>(w.out, c, v, w.vec);
                 } else {  // ragged last chunk of the window
                     const int valid = nbytes - c * 16;
                     bits &= (1u << valid) - 1u;
                     const uint32_t ww[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
-                        if (j < valid) w.out[c * 16 + j] = static_cast<uint8_t>(ww[j >> 2] >> ((j & 3) * 8));
+                        if (j < valid) store_sample<8, OUTF>(w.out, c * 16 + j, static_cast<int8_t>(ww[j >> 2] >> ((j & 3) * 8)));
                 }
                 if (PW) {
                     // the samples of the window only: the ragged chunk's tail bytes are not its own
@@ -898,17 +955,25 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                     }
                 }
                 flagged += __popc(bits);
+                if (OUTF == 1) {  // fp16: each int16 pair converted in place, same bytes per chunk
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const __half2 hv = __halves2half2(__short2half_rn(static_cast<short>(ww[q] & 0xFFFFu)),
+                                                          __short2half_rn(static_cast<short>(ww[q] >> 16)));
+                        ww[q] = *reinterpret_cast<const uint32_t *>(&hv);
+                    }
+                }
                 if (w.vec && c < nfull) {
                     __stcs(reinterpret_cast<uint4 *>(w.out + c * 16), make_uint4(ww[0], ww[1], ww[2], ww[3]));
                 } else {
-                    int16_t *o = reinterpret_cast<int16_t *>(w.out);
+                    uint16_t *o = reinterpret_cast<uint16_t *>(w.out);
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
-                        if (j < valid) o[c * 8 + j] = static_cast<int16_t>((ww[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu);
+                        if (j < valid) o[c * 8 + j] = static_cast<uint16_t>((ww[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu);
                 }
                 if (mk) mk[c] = static_cast<uint8_t>(bits);
             }
-            if (MODE == 3) noise_append<12, T, PW, K>(sm, w, r, p, lane, c, bits, nlc, pw);
+            if (MODE == 3) noise_append<12, T, PW, K, OUTF>(sm, w, r, p, lane, c, bits, nlc, pw);
         }
         if (mk) {
             for (int c = nchunks + tid; c < 4 * w.mask_words; c += T) mk[c] = 0;
@@ -941,6 +1006,7 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
     constexpr bool APPLY = (MODE & kModeApply) != 0;
     constexpr bool PW = (MODE & kModePower) != 0;
     constexpr bool COPIES = (MODE & kModeCopies) != 0;
+    constexpr int OUTF = (MODE & kModeF16) ? 1 : ((MODE & kModeBF16) ? 2 : 0);
     constexpr int RMODE = MODE & 3;
     const int lane = tid & 31;
     if (!APPLY) {
@@ -963,13 +1029,14 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
     uint32_t f = 0;
     Pow pw = {0u, 0u};
     const KeysPre key{p};
-    if (!STATS && !COPIES) f = phase_replace<BITS, RMODE, T, PW>(sm, w, r, key, tid, &sm.ctl->ncount[par], pw, &sm.ctl->rep);
+    if (!STATS && !COPIES)
+        f = phase_replace<BITS, RMODE, T, PW, KeysPre, OUTF>(sm, w, r, key, tid, &sm.ctl->ncount[par], pw, &sm.ctl->rep);
     if (!STATS && !COPIES && RMODE == 3) {
         if (BITS == 8) {
-            noise_deferred8<T, PW>(sm, w, r, key, tid, f, pw);
+            noise_deferred8<T, PW, KeysPre, OUTF>(sm, w, r, key, tid, f, pw);
         } else {
             named_bar(sm.bar_id, T);  // every flagged position of the window is in the list
-            noise_list<BITS, T, PW>(sm, w, r, key, tid, &sm.ctl->ncount[par], pw);
+            noise_list<BITS, T, PW, KeysPre, OUTF>(sm, w, r, key, tid, &sm.ctl->ncount[par], pw);
         }
     }
     if (COPIES) {

@@ -103,6 +103,7 @@ extern "C" rfi_status rfi_excise_host(rfi_plan_t P, const void *const *in, void 
     }
     if (P->kmom >= 2) return RFI_ERR_UNSUPPORTED;  // Eq. 3 needs every earlier window's MAD
     if (P->power) return RFI_ERR_UNSUPPORTED;      // the chunk kernels do not meter power
+    if (P->out_format != RFI_OUT_SAME) return RFI_ERR_UNSUPPORTED;
     rfi_status rs = plan_check_buffers(P, in, out, mask, counts);
     if (rs != RFI_OK) return rs;
     rs = ensure_pipe(P);

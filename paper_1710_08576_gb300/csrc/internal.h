@@ -25,6 +25,10 @@ constexpr int kModePower = 16;
 // up to kMaxCopies (k, replacement) variants written to their own outputs. The variants come
 // from Params::var; variant v of segment s is segment v * Params::seg_stride + s.
 constexpr int kModeCopies = 32;
+// Flag bits of the fused output format: write the excised samples as fp16 (int8 and 12-bit
+// input) or bf16 (int8 input), the real-valued input a channeliser FFT reads. Both are exact.
+constexpr int kModeF16 = 64;
+constexpr int kModeBF16 = 128;
 constexpr int kMaxCopies = 8;
 
 // One variant of a digital-copy pass.

@@ -240,7 +240,7 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
         bool alive = true;
         for (uint32_t k = 0; k < tl.nw && alive; ++k) {
             const int64_t widx = static_cast<int64_t>(tl.w0) + k;
-            const Win win = make_win(sg, widx, stage + k * sg.W * BPS, BPS);
+            const Win win = make_win(sg, widx, stage + k * sg.W * BPS, (MODE & (kModeF16 | kModeBF16)) ? 2 : BPS);
             const int2 *amd = ((MODE & kModeApply) && tl.nw <= kApplyTileWindows)
                                   ? reinterpret_cast<const int2 *>(gb + L.amd) + s * kApplyTileWindows + k
                                   : nullptr;

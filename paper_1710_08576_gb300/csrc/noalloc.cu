@@ -115,6 +115,8 @@ extern "C" rfi_status rfi_excise_noalloc(const rfi_plan_desc *d, const void *con
     if (d->num_streams > kMaxStreams) return RFI_ERR_UNSUPPORTED;
     if (d->mom_windows < 0 || d->mom_windows > (1 << 20)) return RFI_ERR_INVALID_ARG;
     if (d->mom_windows >= 2) return RFI_ERR_UNSUPPORTED;  // per-window MAD only
+    if (d->out_format != RFI_OUT_SAME) return d->out_format < 0 || d->out_format > 2 ? RFI_ERR_INVALID_ARG
+                                                                                    : RFI_ERR_UNSUPPORTED;
     const int64_t kq = static_cast<int64_t>(std::floor(d->k * 1.4826 * 65536.0 + 0.5));
     if (kq < 1) return RFI_ERR_INVALID_ARG;
     const int S = d->num_streams;

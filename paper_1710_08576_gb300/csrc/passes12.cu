@@ -1,4 +1,5 @@
-// 12-bit instantiations of the Median-of-MAD passes (Eq. 3) and the power-metered excision.
+// 12-bit instantiations of the Median-of-MAD passes (Eq. 3), the power-metered and digital-copy
+// passes and the fused output formats.
 #include "passes_impl.cuh"
 
 namespace rfi {
@@ -8,11 +9,14 @@ cudaError_t launch_persistent_mom_b12(int mode, const Shape &s, int grid, const 
                                       cudaStream_t st) {
     RFI_DISPATCH_MOM(12, dev::persistent_launch_t, mode, s.consumer_warps, s.groups, s, grid, segs, tiles, ntiles,
                      p, counter, inject, st);
+    RFI_DISPATCH_FMT12(dev::persistent_launch_t, mode, s.consumer_warps, s.groups, s, grid, segs, tiles, ntiles, p,
+                      counter, inject, st);
     return cudaErrorInvalidValue;
 }
 
 int persistent_occupancy_mom_b12(int mode, const Shape &s) {
     RFI_DISPATCH_MOM(12, dev::persistent_occ_t, mode, s.consumer_warps, s.groups, s);
+    RFI_DISPATCH_FMT12(dev::persistent_occ_t, mode, s.consumer_warps, s.groups, s);
     return 0;
 }
 

@@ -123,5 +123,26 @@ cudaError_t mom_launch_t(const MomChunk *chunks, int nchunks, const int32_t *D, 
         }                                                               \
     } while (0)
 
+// The fused output formats run with one group of 8 consumer warps: fp16 for both widths,
+// bf16 for int8 only.
+#define RFI_CASES_FMT(BITS, FN, F, ...)                                                         \
+    RFI_CASE_MCG(BITS, FN, (F + 0), 8, 1, __VA_ARGS__) RFI_CASE_MCG(BITS, FN, (F + 1), 8, 1, __VA_ARGS__) \
+    RFI_CASE_MCG(BITS, FN, (F + 2), 8, 1, __VA_ARGS__) RFI_CASE_MCG(BITS, FN, (F + 3), 8, 1, __VA_ARGS__)
+#define RFI_DISPATCH_FMT8(FN, MODE, CW, G, ...)              \
+    do {                                                     \
+        switch (MODE * 1000 + CW * 10 + G) {                 \
+            RFI_CASES_FMT(8, FN, 64, __VA_ARGS__)            \
+            RFI_CASES_FMT(8, FN, 128, __VA_ARGS__)           \
+            default: break;                                  \
+        }                                                    \
+    } while (0)
+#define RFI_DISPATCH_FMT12(FN, MODE, CW, G, ...)             \
+    do {                                                     \
+        switch (MODE * 1000 + CW * 10 + G) {                 \
+            RFI_CASES_FMT(12, FN, 64, __VA_ARGS__)           \
+            default: break;                                  \
+        }                                                    \
+    } while (0)
+
 }  // namespace dev
 }  // namespace rfi

@@ -53,6 +53,12 @@ rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req) {
     const int min_stage = static_cast<int>((maxwb + 127) / 128 * 128);
     s.consumer_warps = (req && req->consumer_warps) ? req->consumer_warps : 8;
     s.groups = (req && req->groups) ? req->groups : 1;
+    if (P->out_format != RFI_OUT_SAME) {  // the output formats are built for one group of 8 warps
+        if ((req && req->groups > 1) || (req && req->consumer_warps && req->consumer_warps != 8))
+            return RFI_ERR_UNSUPPORTED;
+        s.consumer_warps = 8;
+        s.groups = 1;
+    }
     if (P->kmom >= 2 || P->power || P->ncopy > 0) {  // built for one group of 4 or 8 consumer warps
         if ((req && req->groups > 1) || s.consumer_warps > 8) return RFI_ERR_UNSUPPORTED;
         s.groups = 1;
@@ -265,6 +271,7 @@ rfi_status plan_check_buffers(const rfi_plan_s *P, const void *const *in, void *
         if (!in[i] || !out[i]) return RFI_ERR_INVALID_ARG;
         if (P->bits == 12 && ((reinterpret_cast<uintptr_t>(in[i]) | reinterpret_cast<uintptr_t>(out[i])) & 1))
             return RFI_ERR_ALIGNMENT;
+        if (P->out_format != RFI_OUT_SAME && (reinterpret_cast<uintptr_t>(out[i]) & 1)) return RFI_ERR_ALIGNMENT;
         if (mask && mask[i] && (reinterpret_cast<uintptr_t>(mask[i]) & 3)) return RFI_ERR_ALIGNMENT;
         if (counts && counts[i] && (reinterpret_cast<uintptr_t>(counts[i]) & 3)) return RFI_ERR_ALIGNMENT;
     }
@@ -329,6 +336,11 @@ static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_va
     if (d->mom_windows >= 2 && (d->flags & RFI_PLAN_PER_STREAM)) return RFI_ERR_UNSUPPORTED;
     if ((d->flags & RFI_PLAN_POWER) && ((d->flags & RFI_PLAN_PER_STREAM) || d->mom_windows >= 2))
         return RFI_ERR_UNSUPPORTED;
+    if (d->out_format < RFI_OUT_SAME || d->out_format > RFI_OUT_BF16) return RFI_ERR_INVALID_ARG;
+    if (d->out_format != RFI_OUT_SAME &&
+        ((d->flags & (RFI_PLAN_PER_STREAM | RFI_PLAN_POWER)) || d->mom_windows >= 2 || nvar > 0 ||
+         (d->out_format == RFI_OUT_BF16 && d->sample_bits == 12)))
+        return RFI_ERR_UNSUPPORTED;
     // Kq = round_half_up(k * 1.4826 * 2^16) (fixed-point multiple of Eq. 1)
     const int64_t kq = static_cast<int64_t>(std::floor(d->k * 1.4826 * 65536.0 + 0.5));
     if (kq < 1) return RFI_ERR_INVALID_ARG;
@@ -355,6 +367,7 @@ static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_va
     P->seed = d->seed;
     P->kmom = d->mom_windows >= 2 ? d->mom_windows : 0;
     P->power = (d->flags & RFI_PLAN_POWER) != 0;
+    P->out_format = d->out_format;
     P->ncopy = nvar;
     for (int v = 0; v < nvar; ++v) {
         Variant vr;
@@ -428,7 +441,7 @@ static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_va
     if (rs == RFI_OK) rs = plan_build_tiles(P);
     if (rs == RFI_OK) rs = plan_alloc_workspace(P);
     if (rs == RFI_OK && (P->flags & RFI_PLAN_AUTOTUNE) && !(P->flags & RFI_PLAN_PER_STREAM) && P->kmom < 2 &&
-        !P->power && P->ncopy == 0)
+        !P->power && P->ncopy == 0 && P->out_format == RFI_OUT_SAME)
         rs = plan_autotune(P, d->shape);
     if (rs == RFI_OK && (P->flags & RFI_PLAN_GRAPH)) rs = plan_build_graph(P);
     if (rs != RFI_OK) {

@@ -56,6 +56,7 @@ struct rfi_plan_s {
     // RFI_PLAN_POWER: {sum x^2, sum z^2} per window
     bool power = false;
     uint64_t *d_pow = nullptr;
+    int out_format = RFI_OUT_SAME;  // fused output format
     // digital copy: the variants (segment table holds ncopy * S entries)
     int ncopy = 0;
     std::vector<rfi::Variant> variants;
@@ -103,7 +104,8 @@ std::vector<T> part_args(const rfi_plan_s *P, size_t k, T const *all) {
 }
 // Kernel mode of a per-window MAD plan (the power-metered form when RFI_PLAN_POWER is set).
 inline int plan_kernel_mode(const rfi_plan_s *P) {
-    return P->ncopy > 0 ? kModeCopies : (P->mode | (P->power ? kModePower : 0));
+    const int fmt = P->out_format == RFI_OUT_F16 ? kModeF16 : (P->out_format == RFI_OUT_BF16 ? kModeBF16 : 0);
+    return P->ncopy > 0 ? kModeCopies : (P->mode | (P->power ? kModePower : 0) | fmt);
 }
 
 }  // namespace rfi
