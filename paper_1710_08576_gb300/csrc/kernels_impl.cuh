@@ -49,7 +49,10 @@ __host__ __device__ inline Layout layout(int ncopies, int stages, int stage_byte
     const int meta_end = align_up(L.meta + kMaxStages * static_cast<int>(sizeof(StageMeta)), 128);
     const bool noise = ((mode & 3) == 3 || (mode & kModeCopies) != 0) && (mode & kModeStats) == 0;
     L.nlist = noise ? meta_end : 0;
-    const int list_end = noise ? align_up(meta_end + kNoiseList * 2, 128) : meta_end;
+    // int8: one 16-bit mask per 16-byte chunk of the largest window (at most a stage); 12-bit:
+    // the position list
+    const int noise_bytes = BITS == 8 ? align_up(stage_bytes / 8 > 128 ? stage_bytes / 8 : 128, 128) : kNoiseList * 2;
+    const int list_end = noise ? align_up(meta_end + noise_bytes, 128) : meta_end;
     const bool apply = (mode & kModeApply) != 0;
     L.amd = apply ? list_end : 0;
     const int amd_end = apply ? align_up(list_end + kMaxStages * kApplyTileWindows * 8, 128) : list_end;
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(CW * 32) stream_kernel(Seg sg, int64_t w_begin
         if (threadIdx.x == 0) atomicOr(p.status, kStatusLayout);
         return;
     }
-    const Layout L = layout<BITS>(p.ncopies, 1, 0, CW, 1, MODE);
+    const Layout L = layout<BITS>(p.ncopies, 1, align_up(sg.W * Geo<BITS>::kBps, 128), CW, 1, MODE);  // as the host
     const Shm sm = group_view<BITS>(smem, L, 0, p.ncopies);
     const int tid = threadIdx.x;
     uint8_t *buf = smem + L.stage;
