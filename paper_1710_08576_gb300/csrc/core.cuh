@@ -204,7 +204,14 @@ struct Geo {
     static constexpr int kBps = BITS == 8 ? 1 : 2;          // bytes per sample
     static constexpr int kLo = BITS == 8 ? -128 : -2048;
     static constexpr int kHi = BITS == 8 ? 127 : 2047;
-    static constexpr int kCumWords = kBins + kBins / 32;     // padded: index b + b/32
+    // cumulative counts, laid out against bank conflicts: 8-bit padded, b + b/32; 12-bit
+    // swizzled in place: within each row of 16 bins the 16-byte group q sits at q ^ (row/2 mod 4),
+    // so that both a warp's consecutive 16-byte writes and its threads' reads of their own rows
+    // touch 8 distinct bank groups per 8 lanes
+    static constexpr int kCumWords = BITS == 8 ? kBins + kBins / 32 : kBins;
+    __host__ __device__ static constexpr int cum_index(int b) {
+        return BITS == 8 ? b + (b >> 5) : (b & ~15) | ((((b >> 2) ^ (b >> 5)) & 3) << 2) | (b & 3);
+    }
     static constexpr int kChunkSamples = 16 / kBps;          // samples per 16-byte chunk
     // 8-bit, one consumer group: a 32 KiB table of 128-byte rows (raw byte u -> row u, lane l
     // -> word l). 8-bit, two groups: one 64 KiB table of 256-byte rows shared by both (group g
@@ -441,35 +448,53 @@ __device__ __forceinline__ void phase_reduce_scan8(const Shm &sm, int tid, RowSu
 template <int T>
 __device__ __forceinline__ void phase_reduce_scan12(const Shm &sm, int tid, int n) {
     constexpr int B = 4096;
-    constexpr int BPT = B / T;
-    uint32_t *h = reinterpret_cast<uint32_t *>(sm.hist);
+    constexpr int BPT = B / T;  // consecutive bins per thread in the scan
+    static_assert(BPT % 4 == 0, "whole 16-byte groups of bins per thread");
+    uint4 *h4 = reinterpret_cast<uint4 *>(sm.hist);
     uint32_t *cum = sm.cum;
     const int nc = sm.ncopies;
-    for (int b = tid; b < B; b += T) {
-        uint32_t s = 0;
-        for (int c = 0; c < nc; ++c) {
-            s += h[c * B + b];
-            h[c * B + b] = 0u;
+    // fold the copies (and clear them) four bins at a time, coalesced
+    for (int i4 = tid; i4 < B / 4; i4 += T) {
+        uint4 s = h4[i4];
+        h4[i4] = make_uint4(0u, 0u, 0u, 0u);
+        for (int c = 1; c < nc; ++c) {
+            const uint4 a = h4[c * (B / 4) + i4];
+            h4[c * (B / 4) + i4] = make_uint4(0u, 0u, 0u, 0u);
+            s.x += a.x;
+            s.y += a.y;
+            s.z += a.z;
+            s.w += a.w;
         }
-        cum[pad32(b)] = s;
+        *reinterpret_cast<uint4 *>(cum + Geo<12>::cum_index(4 * i4)) = s;
     }
     named_bar(sm.bar_id, T);
     uint32_t v[BPT];
     uint32_t run = 0;
 #pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        run += cum[pad32(tid * BPT + i)];
-        v[i] = run;
+    for (int q = 0; q < BPT / 4; ++q) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(cum + Geo<12>::cum_index(tid * BPT + 4 * q));
+        run += a.x;
+        v[4 * q] = run;
+        run += a.y;
+        v[4 * q + 1] = run;
+        run += a.z;
+        v[4 * q + 2] = run;
+        run += a.w;
+        v[4 * q + 3] = run;
     }
     const uint32_t excl = block_offsets<T>(sm, run, tid);
     const uint32_t half = static_cast<uint32_t>((n + 1) >> 1);
     uint32_t prev = excl;
 #pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        const uint32_t c = v[i] + excl;
-        cum[pad32(tid * BPT + i)] = c;
-        if (c >= half && prev < half) sm.ctl->mb = tid * BPT + i;
-        prev = c;
+    for (int q = 0; q < BPT / 4; ++q) {
+        uint32_t c[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            c[k] = v[4 * q + k] + excl;
+            if (c[k] >= half && prev < half) sm.ctl->mb = tid * BPT + 4 * q + k;
+            prev = c[k];
+        }
+        *reinterpret_cast<uint4 *>(cum + Geo<12>::cum_index(tid * BPT + 4 * q)) = make_uint4(c[0], c[1], c[2], c[3]);
     }
 }
 
@@ -546,7 +571,7 @@ __device__ __forceinline__ void phase_search(const Shm &sm, int n, int lane, int
     const int d = warp_search<B>(lane, [&](int dd) {
         const int hi = mb + dd < B - 1 ? mb + dd : B - 1;
         const int lo = mb - dd - 1;
-        const uint32_t f = cum[pad32(hi)] - (lo >= 0 ? cum[pad32(lo)] : 0u);
+        const uint32_t f = cum[Geo<BITS>::cum_index(hi)] - (lo >= 0 ? cum[Geo<BITS>::cum_index(lo)] : 0u);
         return f >= half;
     });
     if (lane == 0) sm.ctl->rep = make_rep<BITS>(mb - Geo<BITS>::kOffset, d, kq, cval);
