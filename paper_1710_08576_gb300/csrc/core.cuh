@@ -556,6 +556,16 @@ __device__ __forceinline__ RepShared make_rep(int32_t M, int32_t d, int64_t kq, 
         r.ulo7 = (ub & 0x7Fu) * 0x01010101u;
         r.usmall = ub < 128u ? ~0u : 0u;
         r.unone = ub > 255u ? 1u : 0u;
+    } else {
+        // 12-bit, two samples per word (see rep12_word): u = x + 2048 per 16-bit half
+        const uint32_t mb = static_cast<uint32_t>(r.M + 2048);
+        const uint32_t tt = static_cast<uint32_t>(r.t);  // <= 4096
+        r.mb4 = (mb + tt) * 0x00010001u;                  // upper bound, u >= it flags
+        r.tlo7 = (0x8000u + mb - tt) * 0x00010001u;       // 0x8000 + lower bound, u <= it flags
+        r.c4 = (static_cast<uint32_t>(cval) & 0xFFFFu) * 0x00010001u;
+        r.hi4 = (static_cast<uint32_t>(r.hiv) & 0xFFFFu) * 0x00010001u;
+        r.lo4 = (static_cast<uint32_t>(r.lov) & 0xFFFFu) * 0x00010001u;
+        r.tsmall = r.ulo7 = r.usmall = r.unone = 0u;
     }
     return r;
 }
@@ -625,6 +635,29 @@ __device__ __forceinline__ uint32_t rep8_word(uint32_t w, const Rep8 &k, uint32_
         rep = (k.hi4 & up) | (k.lo4 & ~up);
     }
     return (w & ~f) | (rep & f);
+}
+
+// Two 12-bit samples (int16 halves of w, in range): returns the output word and sets fm to the
+// flag bits (bit 15 / bit 31). With u = x + 2048 (12 bits) per half and bounds lo = M + 2048 - t,
+// hi = M + 2048 + t: x is flagged iff u >= hi or u <= lo (Eq. 2 with |x - M| >= t). Per half,
+// (u | 0x8000) - hi has bit 15 set iff u >= hi, and (0x8000 + lo) - u iff u <= lo; no borrow
+// crosses the halves because every operand is below 2^13. A flag moved down to bit 0 / 16 and
+// multiplied by 0xFFFF gives the half's select mask.
+template <int MODE>
+__device__ __forceinline__ uint32_t rep12_word(uint32_t w, uint32_t hi2, uint32_t lo2x, uint32_t c2, uint32_t h2,
+                                               uint32_t l2, uint32_t &fm) {
+    const uint32_t u = (w ^ 0x08000800u) & 0x0FFF0FFFu;
+    const uint32_t up = (u | 0x80008000u) - hi2;   // bit 15 / 31: u >= hi
+    const uint32_t dn = lo2x - u;                   // bit 15 / 31: u <= lo
+    fm = (up | dn) & 0x80008000u;
+    const uint32_t m = (fm >> 15) * 0xFFFFu;  // 0xFFFF in a flagged half
+    uint32_t z = 0u;
+    if (MODE == 1) z = c2;
+    if (MODE == 2) {
+        const uint32_t ma = ((up >> 15) & 0x00010001u) * 0xFFFFu;
+        z = (h2 & ma) | (l2 & ~ma);
+    }
+    return (w & ~m) | (z & m);
 }
 
 // Mask bits of a 16-sample chunk from its four flag words (0x00/0xFF bytes), sample j -> bit j.
@@ -952,6 +985,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
     } else {
         uint8_t *mk = reinterpret_cast<uint8_t *>(w.mask);
         const int32_t t = r.t;
+        const RepShared k12 = *rsrc;
         for (int base = warp * 32; base < nchunks; base += T) {
             const int c = base + lane;
             uint32_t bits = 0;
@@ -959,6 +993,20 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 const uint4 v = d4[c];
                 uint32_t ww[4] = {v.x, v.y, v.z, v.w};
                 const int valid = c < nfull ? 8 : ((nbytes - c * 16) >> 1);  // samples in the window
+                if (!PW) {
+                    if (r.active) {
+                        uint32_t f[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) ww[q] = rep12_word<MODE>(ww[q], k12.mb4, k12.tlo7, k12.c4, k12.hi4,
+                                                                             k12.lo4, f[q]);
+                        // flag bits 15 / 31 of the four words -> bits 0..7 (sample order)
+                        const uint32_t g0 = __byte_perm(f[0], f[1], 0x7531u) & 0x80808080u;
+                        const uint32_t g1 = __byte_perm(f[2], f[3], 0x7531u) & 0x80808080u;
+                        bits = ((g0 * 0x00204081u) >> 28) | (((g1 * 0x00204081u) >> 28) << 4);
+                        // samples past the window (a ragged last chunk) are neither flagged nor stored
+                        if (valid < 8) bits &= (1u << valid) - 1u;
+                    }
+                } else {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int sh = (j & 1) * 16;
@@ -978,6 +1026,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                         pw.x += static_cast<uint32_t>(x * x);
                         pw.z += static_cast<uint32_t>(zo * zo);
                     }
+                }
                 }
                 flagged += __popc(bits);
                 if (OUTF == 1) {  // fp16: each int16 pair converted in place, same bytes per chunk
