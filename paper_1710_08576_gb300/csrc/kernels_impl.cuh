@@ -2,6 +2,7 @@
 // one-CTA-per-window kernel. Instantiated per sample width in kernels8.cu / kernels12.cu.
 #pragma once
 
+#include <cstddef>
 #include <mutex>
 
 #include "core.cuh"
@@ -107,8 +108,14 @@ __device__ __forceinline__ Win make_win(const Seg &sg, int64_t w, const uint8_t 
 // descriptor, arms the stage's full barrier with the byte count and issues one bulk copy.
 // The group's consumers wait on the full barrier, process the tile's windows, and release the
 // stage through its empty barrier. All waits are bounded.
+// Resident CTAs per SM that the register budget is sized for (0: left to the compiler). One
+// group of 8 + 1 warps runs three CTAs per SM, which its shared memory allows and 72 registers
+// a thread fit; the hint keeps the allocator from cutting registers for a fourth CTA that the
+// shared memory never grants.
+constexpr int min_ctas_per_sm(int cw, int g) { return g != 1 ? 0 : (cw == 8 ? 3 : (cw == 4 ? 4 : 0)); }
+
 template <int BITS, int MODE, int CW, int G>
-__global__ void __launch_bounds__(G *(CW + 1) * 32)
+__global__ void __launch_bounds__(G *(CW + 1) * 32, min_ctas_per_sm(CW, G))
 persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, int ntiles, Params p,
                   int stages, int stage_bytes, int dynamic_tiles, unsigned *counter, int inject_timeout) {
     constexpr int T = CW * 32;          // consumer threads per group
@@ -148,6 +155,47 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
     const unsigned nq = gridDim.x * G;
     if (warp == CW) {
         // ---------------- copy warp
+        // The tile descriptors are fetched three iterations deep, one dependent step per
+        // iteration: the tile index of iteration it + 3 (the atomic of the dynamic queue), the
+        // tile words of it + 2 and the segment words of it + 1. Every value is used one
+        // iteration after it was requested, so the refill of a stage waits on no global round
+        // trip but its own bulk copy. Lane l < 4 holds word l of the tile, lanes 4..27 word
+        // l - 4 of its segment: the stage descriptor as it is stored.
+        constexpr unsigned kAll = 0xFFFFFFFFu;
+        static_assert(sizeof(Tile) == 16 && sizeof(Seg) == 96, "descriptor copy layout");
+        constexpr int kLaneW0 = offsetof(Tile, w0) / 4, kLaneNw = offsetof(Tile, nw) / 4;
+        constexpr int kLaneBytes = offsetof(Tile, bytes) / 4;
+        constexpr int kLaneIn = 4 + offsetof(Seg, in) / 4, kLaneMed = 4 + offsetof(Seg, med) / 4;
+        constexpr int kLaneMad = 4 + offsetof(Seg, mad) / 4, kLaneW = 4 + offsetof(Seg, W) / 4;
+        constexpr int kLaneVec = 4 + offsetof(Seg, vec) / 4;
+        const uint32_t *tile_w = reinterpret_cast<const uint32_t *>(tiles);
+        const uint32_t *seg_w = reinterpret_cast<const uint32_t *>(segs);
+        auto grab = [&](int i) -> int {  // lane 0: the group's tile of iteration i
+            return dynamic_tiles == 1 ? static_cast<int>(atomicAdd(counter, 1u))
+                                      : static_cast<int>(qid + static_cast<unsigned>(i) * nq);
+        };
+        auto tile_word = [&](int t) -> uint32_t {
+            return (t < ntiles && lane < 4) ? tile_w[4 * t + lane] : 0u;
+        };
+        auto desc_word = [&](int t, uint32_t tw) -> uint32_t {
+            const uint32_t si = __shfl_sync(kAll, tw, 0);
+            return lane < 4 ? tw : ((t < ntiles && lane < 28) ? seg_w[24 * si + (lane - 4)] : 0u);
+        };
+        auto ptr = [&](uint32_t dw, int l) -> uint64_t {
+            return static_cast<uint64_t>(__shfl_sync(kAll, dw, l)) |
+                   (static_cast<uint64_t>(__shfl_sync(kAll, dw, l + 1)) << 32);
+        };
+        int g0 = 0, g1 = 0;
+        if (lane == 0) {
+            g0 = grab(0);
+            g1 = g0 < ntiles ? grab(1) : ntiles;
+        }
+        int t0 = __shfl_sync(kAll, g0, 0);
+        int t1 = __shfl_sync(kAll, g1, 0);
+        uint32_t dw = desc_word(t0, tile_word(t0));  // descriptor of iteration it
+        uint32_t tw1 = tile_word(t1);                // tile words of iteration it + 1
+        int pend = 0;                                // lane 0: tile index of iteration it + 2
+        if (lane == 0) pend = t1 < ntiles ? grab(2) : ntiles;
         int issued = 0;  // iterations whose full barrier was armed
         for (int it = 0;; ++it) {
             const int s = it % stages;
@@ -155,7 +203,7 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
             if (u > 0) {
                 int ok = 1;
                 if (lane == 0) ok = mbar_wait_bounded(empty_bar(s), (u - 1) & 1, kWaitTimeoutNs);
-                ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+                ok = __shfl_sync(kAll, ok, 0);
                 if (!ok) {
                     if (lane == 0) {
                         atomicOr(p.status, kStatusTimeout);
@@ -165,11 +213,7 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
                 }
             }
             if (*reinterpret_cast<volatile uint32_t *>(&sm.ctl->abort)) break;
-            int t = 0;
-            if (lane == 0)
-                t = dynamic_tiles == 1 ? static_cast<int>(atomicAdd(counter, 1u))
-                                       : static_cast<int>(qid + static_cast<unsigned>(it) * nq);
-            t = __shfl_sync(0xFFFFFFFFu, t, 0);
+            const int t = t0;
             issued = it + 1;
             if (t >= ntiles) {
                 if (lane == 0) {
@@ -178,22 +222,25 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
                 }
                 break;
             }
-            const Tile tl = tiles[t];
-            const Seg &sg = segs[tl.seg];
-            // the stage descriptor: lanes 0..3 copy the tile, lanes 4..27 the segment
-            static_assert(sizeof(Tile) == 16 && sizeof(Seg) == 96, "descriptor copy layout");
+            const uint32_t w0 = __shfl_sync(kAll, dw, kLaneW0), nw = __shfl_sync(kAll, dw, kLaneNw);
+            const uint32_t tbytes = __shfl_sync(kAll, dw, kLaneBytes);
+            const uint8_t *in = reinterpret_cast<const uint8_t *>(ptr(dw, kLaneIn));
+            const int32_t W = static_cast<int32_t>(__shfl_sync(kAll, dw, kLaneW));
+            const bool vec = __shfl_sync(kAll, dw, kLaneVec) != 0u;
             uint32_t *md = reinterpret_cast<uint32_t *>(&meta[s]);
-            if (lane < 4) md[lane] = reinterpret_cast<const uint32_t *>(tiles + t)[lane];
-            else if (lane < 28) md[lane] = reinterpret_cast<const uint32_t *>(segs + tl.seg)[lane - 4];
+            if (lane < 28) md[lane] = dw;
             uint8_t *stage = stage0 + s * stage_bytes;
-            const bool vec = sg.vec != 0;
-            if ((MODE & kModeApply) && static_cast<uint32_t>(lane) < tl.nw && tl.nw <= kApplyTileWindows) {
+            if (MODE & kModeApply) {
                 // the centre and dispersion of the tile's windows ride along with the stage
-                int2 *amd = reinterpret_cast<int2 *>(gb + L.amd) + s * kApplyTileWindows;
-                amd[lane] = make_int2(sg.med[tl.w0 + lane], sg.mad[tl.w0 + lane]);
+                const int32_t *med = reinterpret_cast<const int32_t *>(ptr(dw, kLaneMed));
+                const int32_t *mad = reinterpret_cast<const int32_t *>(ptr(dw, kLaneMad));
+                if (static_cast<uint32_t>(lane) < nw && nw <= kApplyTileWindows) {
+                    int2 *amd = reinterpret_cast<int2 *>(gb + L.amd) + s * kApplyTileWindows;
+                    amd[lane] = make_int2(med[w0 + lane], mad[w0 + lane]);
+                }
             }
-            const uint8_t *src = sg.in + static_cast<int64_t>(tl.w0) * sg.W * BPS;
-            const uint32_t bulk = vec ? (tl.bytes & ~15u) : 0u, rem = tl.bytes & 15u;
+            const uint8_t *src = in + static_cast<int64_t>(w0) * W * BPS;
+            const uint32_t bulk = vec ? (tbytes & ~15u) : 0u, rem = tbytes & 15u;
             if (vec && static_cast<uint32_t>(lane) < rem) stage[bulk + lane] = src[bulk + lane];
             __syncwarp();
             if (lane == 0) {
@@ -201,6 +248,13 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
                 mbar_arrive_tx(full_bar(s), bulk);
                 if (bulk) bulk_g2s(smem_addr(stage), src, bulk, full_bar(s));
             }
+            // advance the descriptor pipeline by one iteration
+            dw = desc_word(t1, tw1);
+            const int t2 = __shfl_sync(kAll, pend, 0);
+            tw1 = tile_word(t2);
+            if (lane == 0) pend = t2 < ntiles ? grab(it + 3) : ntiles;
+            t0 = t1;
+            t1 = t2;
         }
         // drain: every armed stage has landed before the copy warp leaves
         if (lane == 0) {
