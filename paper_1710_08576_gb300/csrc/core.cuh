@@ -245,6 +245,12 @@ struct CopyShared {
     uint32_t ncount[2 * kMaxCopies];   // 12-bit digital-noise list entries, by variant and parity
 };
 
+// Apply passes over whole tiles: the thresholds and flag counts of the tile's windows.
+struct ApplyTile {
+    RepShared rep[kApplyTileWindows];
+    uint32_t count[kApplyTileWindows];
+};
+
 struct Ctl {
     uint32_t warp_tot[32];
     RepShared rep;       // threshold and replacement values of the current window
@@ -276,6 +282,7 @@ struct Shm {
     CopyShared *cp;      // digital copy: per-variant state (or null)
     uint16_t *nlist;     // digital noise work area (or null): int8, the window's chunk flag masks;
                          // 12-bit, the positions of its flagged samples
+    ApplyTile *at;       // apply passes: the current tile's thresholds and counts (or null)
 };
 
 // Capacity of the digital-noise work area (16-bit entries: int8 chunk masks of windows up to
@@ -1194,6 +1201,125 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
             if (!APPLY && sg.mad) sg.mad[widx] = r.D;
             sm.ctl->flagged += cnt;
             if (BITS == 12 && atomicExch(&sm.ctl->err[par], 0u)) atomicOr(p.status, kStatusSampleRange);
+            if (release_bar) mbar_arrive(release_bar);
+        }
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------ apply pass over a tile
+// The apply pass (Eq. 1 and Eq. 2 around each window's given M with its given dispersion, as
+// for the median of MADs of Eq. 3) over a whole tile of nw full int8 windows of one segment,
+// W = 2^lw >= 512 samples each, 16-byte aligned. One barrier for the tile's thresholds (thread
+// k builds window k's), then the replace pass over all of the tile's chunks: a warp's round of
+// 32 chunks lies in one window, whose flag count takes one shared atomic. Digital noise is the
+// deferred scheme of noise_deferred8 over the tile, each sample taking its window's M and
+// spread. The last warp writes the tile's counts and releases the stage. Against one window
+// at a time this saves three barriers per window and keeps every thread busy on windows of
+// 4096 samples, which give 256 threads one chunk each.
+template <int MODE, int T>
+__device__ bool process_tile_apply8(const Shm &sm, const uint8_t *stage, const Tile &tl, const Seg &sg,
+                                    const int2 *amd, const Params &p, int tid, int par, int lw,
+                                    uint32_t release_bar, bool stage_ok) {
+    constexpr int NW = T / 32;
+    constexpr int RMODE = MODE & 3;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nw = static_cast<int>(tl.nw);
+    // every thread has finished the previous tile or window (its thresholds, counts, noise
+    // work area) before this barrier
+    if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
+    RepShared *reps = sm.at->rep;
+    uint32_t *cnt = sm.at->count;
+    if (tid < nw) reps[tid] = make_rep<8>(amd[tid].x, amd[tid].y, p.kq, p.cval);
+    named_bar(sm.bar_id, T);
+
+    const int lcw = lw - 4;  // log2 of the chunks per window
+    const int nchunks = nw << lcw;
+    const uint4 *d4 = reinterpret_cast<const uint4 *>(stage);
+    uint8_t *out = sg.out + (static_cast<int64_t>(tl.w0) << lw);
+    uint16_t *mk = sg.mask ? reinterpret_cast<uint16_t *>(sg.mask + static_cast<int64_t>(tl.w0) * sg.mask_words)
+                           : nullptr;
+    uint32_t own = 0;  // this thread's flagged samples (noise numbering)
+    for (int c0 = warp * 32; c0 < nchunks; c0 += T) {
+        const int k = c0 >> lcw;
+        const RepShared &rk = reps[k];
+        const uint4 *rq = reinterpret_cast<const uint4 *>(&rk);
+        const uint4 q2 = rq[2], q3 = rq[3], q4 = rq[4];
+        Rep8 k8;
+        k8.mb4 = q2.x;
+        k8.tlo7 = q2.y;
+        k8.tsmall = q2.z;
+        k8.c4 = q2.w;
+        k8.hi4 = q3.x;
+        k8.lo4 = q3.y;
+        k8.ulo7 = q3.z;
+        k8.usmall = q3.w;
+        k8.unone = q4.x;
+        const int c = c0 + lane;
+        uint4 v = d4[c];
+        uint32_t bits = 0;
+        if (rk.active) {
+            uint32_t f0, f1, f2, f3;
+            v.x = rep8_word<RMODE>(v.x, k8, f0);
+            v.y = rep8_word<RMODE>(v.y, k8, f1);
+            v.z = rep8_word<RMODE>(v.z, k8, f2);
+            v.w = rep8_word<RMODE>(v.w, k8, f3);
+            bits = chunk_bits(f0, f1, f2, f3);
+        }
+        store_chunk8<0>(out, c, v, true);
+        if (mk) mk[c] = static_cast<uint16_t>(bits);
+        if (RMODE == 3) sm.nlist[c] = static_cast<uint16_t>(bits);
+        own += __popc(bits);
+        const uint32_t wf = __reduce_add_sync(0xFFFFFFFFu, __popc(bits));
+        if (lane == 0 && wf) atomicAdd(&cnt[k], wf);
+    }
+
+    if (RMODE == 3) {
+        // number the tile's flagged samples by (owner thread, chunk, bit), as noise_deferred8
+        const uint32_t first = block_offsets<T>(sm, own, tid);  // group barrier inside
+        uint32_t total = 0;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) total += sm.ctl->warp_tot[i];
+        uint16_t *firsts = reinterpret_cast<uint16_t *>(sm.cum);
+        firsts[tid] = static_cast<uint16_t>(first < 65535u ? first : 65535u);
+        named_bar(sm.bar_id, T);
+        const KeysPre key{p};
+        const int64_t abs0 = sg.abs0 + (static_cast<int64_t>(tl.w0) << lw);
+        for (uint32_t q = static_cast<uint32_t>(tid); q < total; q += T) {
+            int u = 0;
+#pragma unroll
+            for (int step = T / 2; step >= 1; step >>= 1)
+                if (firsts[u + step] <= q) u += step;
+            uint32_t j = q - firsts[u];
+            int c = u;
+            uint32_t b = sm.nlist[c];
+            while (j >= static_cast<uint32_t>(__popc(b)) && c + T < nchunks) {
+                j -= __popc(b);
+                c += T;
+                b = sm.nlist[c];
+            }
+            if (j >= static_cast<uint32_t>(__popc(b))) continue;
+            const int pos = c * 16 + nth_set_bit(b, static_cast<int>(j));
+            const RepShared &rk = reps[pos >> lw];
+            const int32_t z = noise_value(rk.M, rk.sigq, key, sg.stream_id, abs0 + pos, Geo<8>::kLo, Geo<8>::kHi);
+            out[pos] = static_cast<uint8_t>(z);
+        }
+    }
+
+    if (lane == 0) {
+        __threadfence_block();
+        if (atomicAdd(&sm.ctl->done[par], 1u) == NW - 1) {
+            // last warp of the tile: every count is in and every read of the stage is done
+            __threadfence_block();
+            sm.ctl->done[par] = 0u;
+            unsigned long long tot = 0ull;
+            for (int k = 0; k < nw; ++k) {
+                const uint32_t ck = cnt[k];
+                cnt[k] = 0u;
+                if (sg.counts) sg.counts[tl.w0 + k] = ck;
+                tot += ck;
+            }
+            sm.ctl->flagged += tot;
             if (release_bar) mbar_arrive(release_bar);
         }
     }

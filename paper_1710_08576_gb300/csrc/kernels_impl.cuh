@@ -34,6 +34,7 @@ struct Layout {
     int cum, ctl, bar, meta;  // offsets inside a group block
     int nlist;                // digital-noise position list inside a group block (0: none)
     int amd;                  // apply passes: per stage, {M, dispersion} of its windows (0: none)
+    int atile;                // apply passes: thresholds and counts of the current tile (0: none)
     int cps;                  // digital copy: per-variant state inside a group block (0: none)
     int stage;      // first stage buffer; group g stage s at stage + (g * stages + s) * stage_bytes
     int total;
@@ -56,7 +57,8 @@ __host__ __device__ inline Layout layout(int ncopies, int stages, int stage_byte
     const int list_end = noise ? align_up(meta_end + noise_bytes, 128) : meta_end;
     const bool apply = (mode & kModeApply) != 0;
     L.amd = apply ? list_end : 0;
-    const int amd_end = apply ? align_up(list_end + kMaxStages * kApplyTileWindows * 8, 128) : list_end;
+    L.atile = apply ? align_up(list_end + kMaxStages * kApplyTileWindows * 8, 128) : 0;
+    const int amd_end = apply ? align_up(L.atile + static_cast<int>(sizeof(ApplyTile)), 128) : list_end;
     const bool copies = (mode & kModeCopies) != 0;
     L.cps = copies ? amd_end : 0;
     L.grp_size = copies ? align_up(amd_end + static_cast<int>(sizeof(CopyShared)), 128) : amd_end;
@@ -79,6 +81,7 @@ __device__ __forceinline__ Shm group_view(uint8_t *smem, const Layout &L, int g,
     sm.bar_id = 1 + g;
     sm.nlist = L.nlist ? reinterpret_cast<uint16_t *>(gb + L.nlist) : nullptr;
     sm.cp = L.cps ? reinterpret_cast<CopyShared *>(gb + L.cps) : nullptr;
+    sm.at = L.atile ? reinterpret_cast<ApplyTile *>(gb + L.atile) : nullptr;
     return sm;
 }
 
@@ -295,6 +298,22 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
             }
         }
         bool alive = true;
+        if constexpr (BITS == 8 && (MODE & kModeApply) != 0 && (MODE & ~(kModeApply | 3)) == 0) {
+            // a tile of full windows of 2^lw >= 512 aligned samples goes through in one pass
+            const uint32_t W = static_cast<uint32_t>(sg.W);
+            if (sg.vec && tl.nw <= static_cast<uint32_t>(kApplyTileWindows) && W >= 512u && (W & (W - 1u)) == 0u &&
+                tl.bytes == tl.nw * W) {
+                const int2 *amd = reinterpret_cast<const int2 *>(gb + L.amd) + s * kApplyTileWindows;
+                alive = process_tile_apply8<MODE, T>(sm, stage, tl, sg, amd, p, tid, par, 31 - __clz(static_cast<int>(W)),
+                                                     empty_bar(s), true);
+                par ^= 1;
+                if (!alive) {
+                    timed_out = true;
+                    break;
+                }
+                continue;
+            }
+        }
         for (uint32_t k = 0; k < tl.nw && alive; ++k) {
             const int64_t widx = static_cast<int64_t>(tl.w0) + k;
             const Win win = make_win(sg, widx, stage + k * sg.W * BPS, (MODE & (kModeF16 | kModeBF16)) ? 2 : BPS);
