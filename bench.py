@@ -438,7 +438,7 @@ def run_ours(args):
         d2h = (samples_per_call * esz + sum(m.numel() * 4 for m in h_mask) + windows_per_call * 4) * len(batched)
         e2e = {"value": sum_over_ranks(samples_per_call * len(batched) * e2e_steps) / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-               "path": "rfi_excise_host, pinned host buffers, 32 MiB chunks on 3 streams"}
+               "path": "rfi_excise_host, pinned host buffers, 128 MiB chunks on 3 streams"}
         del h_in, h_out, h_mask, h_cnt
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only)

@@ -182,7 +182,10 @@ RFI_API rfi_status rfi_excise(rfi_plan_t plan, const void *const *in, void *cons
 
 /* Same computation with HOST buffers (pinned or pageable): input is copied to the device in
  * chunks on `stream` and a second internal stream, excised, and copied back, overlapping the
- * three. Synchronous: returns when every output is in host memory. */
+ * three. Synchronous: returns when every output is in host memory. The first call allocates
+ * the plan's staging area: three chunk slots of up to 128 MiB of input each (less when the
+ * streams are shorter), with as much output and their masks and counts; rfi_plan_destroy
+ * frees it. */
 RFI_API rfi_status rfi_excise_host(rfi_plan_t plan, const void *const *in, void *const *out,
                            uint32_t *const *mask, uint32_t *const *counts, void *stream);
 

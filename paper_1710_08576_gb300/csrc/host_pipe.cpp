@@ -13,7 +13,7 @@
 namespace rfi {
 
 namespace {
-constexpr int64_t kChunkTarget = 32ll << 20;  // input bytes per chunk
+constexpr int64_t kChunkTarget = 128ll << 20;  // input bytes per chunk
 }
 
 void plan_release_host_pipe(rfi_plan_s *P) {
