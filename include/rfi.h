@@ -99,6 +99,10 @@ typedef enum { RFI_OUT_SAME = 0, RFI_OUT_F16 = 1, RFI_OUT_BF16 = 2 } rfi_out_for
                                      the improvement metric of Section III-A. Batched form and
                                      per-window MAD only (RFI_ERR_UNSUPPORTED otherwise); fixed
                                      launch shape as for mom_windows >= 2 */
+#define RFI_PLAN_NOISE_PASS 0x40u /* batched noise plans: write the digital noise in a second kernel
+                                     over the flag masks instead of inside the excision kernel
+                                     (same bits; two launches per call). Faster for windows of a
+                                     few thousand samples, slower for densely flagged data */
 #define RFI_PLAN_INJECT_TIMEOUT 0x100u /* test hook: CTA 0 waits on a barrier nothing arrives
                                           on (bounded by 1 ms), latching RFI_ERR_TIMEOUT */
 

@@ -79,7 +79,7 @@ std::string cache_key(const rfi_plan_s *P) {
     std::string k;
     if (cudaGetDeviceProperties(&prop, P->device) == cudaSuccess) k = prop.name;
     char buf[96];
-    std::snprintf(buf, sizeof(buf), "|%d|%d|%d|", P->bits, P->mode, P->S);
+    std::snprintf(buf, sizeof(buf), "|%d|%d|%d|", P->bits, plan_kernel_mode(P), P->S);
     k += buf;
     for (int i = 0; i < P->S; ++i) {
         std::snprintf(buf, sizeof(buf), "%d:%lld,", P->W[i], static_cast<long long>(P->len[i] / P->W[i]));
@@ -146,7 +146,7 @@ rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req) {
         bool hit = it != g_cache.end();
         if (hit) cached = it->second;
         else if (cache_file_lookup(key, &cached)) {
-            hit = persistent_occupancy(P->bits, P->mode, cached) >= cached.ctas_per_sm;
+            hit = persistent_occupancy(P->bits, plan_kernel_mode(P), cached) >= cached.ctas_per_sm;
             if (hit) g_cache[key] = cached;
         }
         if (hit) {
@@ -232,7 +232,7 @@ rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req) {
                             }
                             if (s.stage_bytes > 96 * 1024 && mult > 1) continue;
                             if (grp * (cw + 1) * 32 * ctas > 2048) continue;
-                            if (persistent_smem_bytes(P->bits, P->mode, s) * ctas > 228u * 1024u) continue;
+                            if (persistent_smem_bytes(P->bits, plan_kernel_mode(P), s) * ctas > 228u * 1024u) continue;
                             cands.push_back(s);
                         }
     if (cands.empty()) return RFI_ERR_UNSUPPORTED;
@@ -254,7 +254,7 @@ rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req) {
     std::vector<Tile> cur;
     int cur_stage = -1;
     for (const Shape &s : cands) {
-        if (persistent_occupancy(P->bits, P->mode, s) < s.ctas_per_sm) {
+        if (persistent_occupancy(P->bits, plan_kernel_mode(P), s) < s.ctas_per_sm) {
             cudaGetLastError();
             continue;
         }
@@ -277,7 +277,7 @@ rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req) {
         for (int rep = 0; rep < 4 && ok; ++rep) {
             ok = cudaMemsetAsync(sc.ctr, 0, sizeof(DevCounters), st) == cudaSuccess;
             ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
-            ok = ok && launch_persistent(P->bits, P->mode, s, grid, sc.segs, sc.tiles, nt, p, &sc.ctr->tile_counter,
+            ok = ok && launch_persistent(P->bits, plan_kernel_mode(P), s, grid, sc.segs, sc.tiles, nt, p, &sc.ctr->tile_counter,
                                          0, st) == cudaSuccess;
             ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
             float ms = 0;

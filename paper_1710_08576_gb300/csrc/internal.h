@@ -143,6 +143,14 @@ struct MomChunk {
 cudaError_t launch_mom(int bits, const MomChunk *chunks, int nchunks, const int32_t *D, int32_t *Mm, int kmom,
                        cudaStream_t st);
 
+// Digital noise as a second pass over segments whose excision pass wrote 0 at the flagged
+// samples, the flag mask and every window's M and D (segments of fewer than 2^31 samples).
+// Segment s covers blocks [fblk[s], fblk[s + 1]) of kFillBlockWords mask words; nblk = fblk[nseg].
+constexpr int kFillBlockWords = 64;
+int noise_fill_grid(int sm_count);
+cudaError_t launch_noise_fill(int bits, const Seg *segs, int nseg, const uint32_t *fblk, uint32_t nblk, const Params &p,
+                              int grid, cudaStream_t st);
+
 // Write n (<= kSegBatch) segment descriptors to dst (device) from kernel parameters.
 constexpr int kSegBatch = 32;
 cudaError_t launch_write_segs(Seg *dst, const Seg *src_host, int n, cudaStream_t st);

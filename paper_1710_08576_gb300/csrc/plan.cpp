@@ -136,7 +136,18 @@ rfi_status plan_alloc_workspace(rfi_plan_s *P) {
     const size_t mc_b = mom ? al(sizeof(MomChunk) * P->mchunks.size()) : 0;
     const size_t pw_b = P->power ? al(2 * sizeof(uint64_t) * P->total_windows) : 0;
     const size_t var_b = al(sizeof(Variant) * P->variants.size());
-    P->ws_bytes = seg_b + tile_b + (mom ? 3 : 2) * md_b + mc_b + pw_b + var_b + ctr_b;
+    std::vector<uint32_t> fblk;
+    if (P->fill) {
+        fblk.push_back(0);
+        for (int i = 0; i < P->S; ++i) {
+            const int64_t words = P->nwin[i] * ((P->W[i] + 31) / 32);
+            fblk.push_back(fblk.back() + static_cast<uint32_t>((words + kFillBlockWords - 1) / kFillBlockWords));
+        }
+        P->nfblk = fblk.back();
+        P->fill_grid = noise_fill_grid(P->sm_count);
+    }
+    const size_t fb_b = al(sizeof(uint32_t) * fblk.size());
+    P->ws_bytes = seg_b + tile_b + (mom ? 3 : 2) * md_b + mc_b + pw_b + var_b + fb_b + ctr_b;
     if (P->ws) cudaFree(P->ws);
     P->ws = nullptr;
     if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
@@ -165,6 +176,10 @@ rfi_status plan_alloc_workspace(rfi_plan_s *P) {
         RFI_CUDA(cudaMemcpy(P->d_var, P->variants.data(), sizeof(Variant) * P->variants.size(),
                             cudaMemcpyHostToDevice));
     }
+    if (P->fill) {
+        P->d_fblk = reinterpret_cast<uint32_t *>(b + ctr_b + seg_b + tile_b + 2 * md_b + mc_b + pw_b + var_b);
+        RFI_CUDA(cudaMemcpy(P->d_fblk, fblk.data(), sizeof(uint32_t) * fblk.size(), cudaMemcpyHostToDevice));
+    }
     P->segs_valid = false;
     return RFI_OK;
 }
@@ -190,8 +205,10 @@ rfi_status plan_enqueue_batched(rfi_plan_s *P, cudaStream_t st) {
     RFI_CUDA(cudaMemsetAsync(P->d_ctr, 0, sizeof(DevCounters), st));
     const int inject = (P->flags & RFI_PLAN_INJECT_TIMEOUT) ? 1 : 0;
     if (P->kmom < 2) {
+        const Params p = plan_params(P);
         RFI_CUDA(launch_persistent(P->bits, plan_kernel_mode(P), P->shape, P->grid, P->d_segs, P->d_tiles,
-                                   P->ntiles, plan_params(P), &P->d_ctr->tile_counter, inject, st));
+                                   P->ntiles, p, &P->d_ctr->tile_counter, inject, st));
+        if (P->fill) RFI_CUDA(launch_noise_fill(P->bits, P->d_segs, P->S, P->d_fblk, P->nfblk, p, P->fill_grid, st));
         return RFI_OK;
     }
     // Median of MAD (Eq. 3): M and D of every window, the sliding median of the MADs, then Eq. 1
@@ -240,6 +257,7 @@ std::vector<Seg> plan_segs(const rfi_plan_s *P, const void *const *in, void *con
         g.in = static_cast<const uint8_t *>(in[i]);
         g.out = static_cast<uint8_t *>(out[i]);
         g.mask = mask ? mask[i] : nullptr;
+        if (P->fill && !g.mask) g.mask = P->d_fmask + P->fmask_off[i];  // the fill pass reads the flags
         g.counts = counts ? counts[i] : nullptr;
         g.med = P->d_med + P->woff[i];
         g.mad = P->d_mad + P->woff[i];
@@ -327,7 +345,7 @@ static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_va
     if (!(d->k > 0.0) || !std::isfinite(d->k) || d->k > 1.0e6) return RFI_ERR_INVALID_ARG;
     if (d->mode < RFI_REPLACE_ZERO || d->mode > RFI_REPLACE_NOISE) return RFI_ERR_INVALID_ARG;
     const uint32_t known = RFI_PLAN_PER_STREAM | RFI_PLAN_BATCHED | RFI_PLAN_GRAPH | RFI_PLAN_AUTOTUNE |
-                           RFI_PLAN_INJECT_TIMEOUT | RFI_PLAN_POWER | RFI_PLAN_NO_SPLIT;
+                           RFI_PLAN_INJECT_TIMEOUT | RFI_PLAN_POWER | RFI_PLAN_NO_SPLIT | RFI_PLAN_NOISE_PASS;
     if (d->flags & ~known) return RFI_ERR_INVALID_ARG;
     if ((d->flags & RFI_PLAN_PER_STREAM) && (d->flags & (RFI_PLAN_BATCHED | RFI_PLAN_GRAPH)))
         return RFI_ERR_INVALID_ARG;
@@ -391,6 +409,12 @@ static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_va
     }
     P->total_windows = total_w;
     P->total_samples = total_s;
+    // RFI_PLAN_NOISE_PASS: digital noise as a second kernel, for batched plain noise plans over
+    // segments of < 2^31 samples (others keep it in the excision kernel)
+    bool short_segs = true;
+    for (int i = 0; i < P->S; ++i) short_segs = short_segs && P->len[i] < (int64_t{1} << 31);
+    P->fill = (P->flags & RFI_PLAN_NOISE_PASS) && P->mode == RFI_REPLACE_NOISE && !(P->flags & RFI_PLAN_PER_STREAM) &&
+              P->kmom < 2 && !P->power && P->ncopy == 0 && P->out_format == RFI_OUT_SAME && short_segs;
 
     rfi_status rs = RFI_OK;
     if (cudaGetDevice(&P->device) != cudaSuccess ||
@@ -473,6 +497,24 @@ rfi_status rfi_excise(rfi_plan_t P, const void *const *in, void *const *out, uin
     rfi_status rs = plan_check_buffers(P, in, out, mask, counts);
     if (rs != RFI_OK) return rs;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (P->fill && !P->d_fmask && !(P->flags & RFI_PLAN_PER_STREAM)) {
+        // the fill pass reads the flags: streams called without a mask use the plan's own
+        bool need = !mask;
+        for (int i = 0; i < P->S && !need; ++i) need = !mask[i];
+        if (need) {
+            P->fmask_off.assign(P->S, 0);
+            int64_t words = 0;
+            for (int i = 0; i < P->S; ++i) {
+                P->fmask_off[i] = words;
+                words += P->nwin[i] * ((P->W[i] + 31) / 32);
+            }
+            if (cudaMalloc(&P->d_fmask, sizeof(uint32_t) * static_cast<size_t>(words)) != cudaSuccess) {
+                cudaGetLastError();
+                P->d_fmask = nullptr;
+                return RFI_ERR_OOM;
+            }
+        }
+    }
     std::vector<Seg> segs = plan_segs(P, in, out, mask, counts);
     P->last_windows = P->total_windows;
     if (P->flags & RFI_PLAN_PER_STREAM) {
@@ -684,7 +726,7 @@ rfi_status rfi_plan_get_info(rfi_plan_t P, rfi_plan_info *info) {
     info->shape.hist_copies = P->shape.hist_copies;
     info->shape.groups = P->shape.groups;
     info->sm_count = P->sm_count;
-    info->kernels_per_call = (P->flags & RFI_PLAN_PER_STREAM) ? P->S : (P->kmom >= 2 ? 3 : 1);
+    info->kernels_per_call = (P->flags & RFI_PLAN_PER_STREAM) ? P->S : (P->kmom >= 2 ? 3 : (P->fill ? 2 : 1));
     return RFI_OK;
 }
 
@@ -695,6 +737,7 @@ rfi_status rfi_plan_destroy(rfi_plan_t P) {
     if (P->gexec) cudaGraphExecDestroy(P->gexec);
     if (P->graph) cudaGraphDestroy(P->graph);
     if (P->ws) cudaFree(P->ws);
+    if (P->d_fmask) cudaFree(P->d_fmask);
     cudaGetLastError();
     delete P;
     return RFI_OK;

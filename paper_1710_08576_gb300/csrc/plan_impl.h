@@ -57,6 +57,14 @@ struct rfi_plan_s {
     bool power = false;
     uint64_t *d_pow = nullptr;
     int out_format = RFI_OUT_SAME;  // fused output format
+    // digital noise as a second pass (noise_fill): the excision pass replaces with 0, then the
+    // fill kernel writes the noise of every flagged sample; d_fblk: S + 1 block offsets
+    bool fill = false;
+    uint32_t *d_fblk = nullptr;
+    uint32_t nfblk = 0;
+    int fill_grid = 0;
+    uint32_t *d_fmask = nullptr;  // flag masks of streams called without one (allocated on demand)
+    std::vector<int64_t> fmask_off;
     // digital copy: the variants (segment table holds ncopy * S entries)
     int ncopy = 0;
     std::vector<rfi::Variant> variants;
@@ -105,7 +113,7 @@ std::vector<T> part_args(const rfi_plan_s *P, size_t k, T const *all) {
 // Kernel mode of a per-window MAD plan (the power-metered form when RFI_PLAN_POWER is set).
 inline int plan_kernel_mode(const rfi_plan_s *P) {
     const int fmt = P->out_format == RFI_OUT_F16 ? kModeF16 : (P->out_format == RFI_OUT_BF16 ? kModeBF16 : 0);
-    return P->ncopy > 0 ? kModeCopies : (P->mode | (P->power ? kModePower : 0) | fmt);
+    return P->ncopy > 0 ? kModeCopies : ((P->fill ? 0 : P->mode) | (P->power ? kModePower : 0) | fmt);
 }
 
 }  // namespace rfi

@@ -10,7 +10,9 @@ from .parity import assert_same, gen_streams, gpu_run, oracle_run
 
 pytestmark = pytest.mark.gpu
 
-FORMS = {"batched": 0, "per_stream": 0x1, "graph": 0x4}
+# "noise_pass": batched noise plans write the digital noise in a second kernel
+# (RFI_PLAN_NOISE_PASS); in the other forms it stays in the excision kernel
+FORMS = {"batched": 0, "per_stream": 0x1, "graph": 0x4, "noise_pass": 0x40}
 
 
 def _run_both(rfi, xs, windows, bits, k, mode, const=0, seed=0, **kw):
@@ -47,7 +49,7 @@ def test_gwb_variants_small(cuda, rfi, form, vi):
     assert totals.flagged == sum(int(r["counts"].sum()) for r in ref)
 
 
-@pytest.mark.parametrize("form", ["batched", "per_stream"])
+@pytest.mark.parametrize("form", ["batched", "per_stream", "noise_pass"])
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_twelve_bit_small(cuda, rfi, form, mode):
     w = workloads.twelve60(nstreams=3)
@@ -64,7 +66,7 @@ def test_uneven_windows_small(cuda, rfi):
     wins = [1024, 2048, 4096, 8192, 16384, 32768, 65536, 1024]
     lens = [int(W * rng.integers(1, 4) + rng.integers(0, W)) for W in wins]
     xs = gen_streams(w, lens)
-    for flags in (0, 0x1, 0x4):
+    for flags in (0, 0x1, 0x4, 0x40):
         got, ref, st, _, _ = _run_both(rfi, xs, wins, 8, 3.0, 3, seed=7, flags=flags)
         assert st == 0
         assert_same(got, ref, "uneven flags %d" % flags)
@@ -106,7 +108,7 @@ def test_twelve_bit_histogram_copies(cuda, rfi, hc, groups):
 
 
 @pytest.mark.parametrize("W", [1, 2, 7, 16, 33, 40, 48, 100, 1000, 65536])
-@pytest.mark.parametrize("form", ["batched", "per_stream"])
+@pytest.mark.parametrize("form", ["batched", "per_stream", "noise_pass"])
 def test_odd_window_lengths(cuda, rfi, W, form):
     p = synth.params(seed=21, sigma=16.0, burst_rate=2e-2, burst_len_max=64, bits=8)
     n = 3 * W + (W // 3) + 1 if W > 1 else 50
@@ -124,11 +126,42 @@ def test_misaligned_and_in_place_buffers(cuda, rfi, bits, offset, in_place):
         pytest.skip("int16 buffers are 2-byte aligned")
     p = synth.params(seed=22, sigma=16.0 if bits == 8 else 120.0, burst_rate=1e-2, burst_len_max=64, bits=bits)
     xs = [synth.fill(p, s, 4 * 4096 + 99) for s in range(3)]
-    for flags in (0, 1):
+    for flags in (0, 1, 0x40):
         got, ref, st, _, _ = _run_both(rfi, xs, [4096] * 3, bits, 3.0, 3, seed=9, flags=flags,
                                        offset=offset, in_place=in_place)
         assert st == 0
         assert_same(got, ref, "offset %d in_place %s" % (offset, in_place))
+
+
+@pytest.mark.parametrize("bits", [8, 12])
+def test_noise_pass_without_caller_masks(cuda, rfi, bits):
+    """A RFI_PLAN_NOISE_PASS plan called without masks (or counts) flags into the plan's own masks
+    for its second pass: the samples equal the oracle's; a later call with masks gives the masks
+    too. Windows divisible by 32, by 2048 and by neither."""
+    import torch
+    p = synth.params(seed=31, sigma=16.0 if bits == 8 else 120.0, burst_rate=1e-2, burst_len_max=64, bits=bits)
+    wins = [4096, 1000, 64, 65536]
+    lens = [5 * 4096 + 17, 7 * 1000 + 999, 300 * 64 + 5, 65536 + 11]
+    xs = [synth.fill(p, s, n) for s, n in enumerate(lens)]
+    ref = oracle_run(xs, wins, bits, 3.0, 3, 0, 12)
+    plan = rfi.Plan(bits, lens, wins, 3.0, 3, 0, 12, rfi.RFI_PLAN_NO_SPLIT | rfi.RFI_PLAN_NOISE_PASS)
+    try:
+        assert plan.info().kernels_per_call == 2
+        ins = [torch.from_numpy(x).cuda() for x in xs]
+        outs = [torch.zeros_like(t) for t in ins]
+        plan.excise(ins, outs)
+        torch.cuda.synchronize()
+        for i, x in enumerate(xs):
+            assert np.array_equal(outs[i].cpu().numpy(), ref[i]["z"]), "stream %d" % i
+        masks = [torch.zeros(plan.mask_words(i), dtype=torch.int32, device="cuda") for i in range(len(xs))]
+        outs2 = [torch.zeros_like(t) for t in ins]
+        plan.excise(ins, outs2, masks, None)
+        torch.cuda.synchronize()
+        for i, x in enumerate(xs):
+            assert np.array_equal(outs2[i].cpu().numpy(), ref[i]["z"]), "stream %d" % i
+            assert np.array_equal(masks[i].cpu().numpy().view(np.uint32), ref[i]["mask"]), "mask %d" % i
+    finally:
+        plan.close()
 
 
 def test_degenerate_windows(cuda, rfi):
@@ -209,7 +242,7 @@ def test_autotuned_plan(cuda, rfi):
 
 
 @pytest.mark.parametrize("bits", [8, 12])
-@pytest.mark.parametrize("form", ["batched", "per_stream"])
+@pytest.mark.parametrize("form", ["batched", "per_stream", "noise_pass"])
 def test_noise_list_overflow(cuda, rfi, bits, form):
     """Windows whose flagged samples outnumber the digital-noise list (4096 entries): 55 % of
     each window sits in a narrow core (small D) and 45 % far outside it, so 7000+ of 16384
