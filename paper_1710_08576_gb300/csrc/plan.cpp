@@ -81,7 +81,7 @@ rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req) {
     s.ctas_per_sm = std::min(want_ctas, occ);
     P->grid_apply = 0;
     if (P->kmom >= 2) {
-        const int occ_apply = persistent_occupancy(P->bits, kModeApply + P->mode, s);
+        const int occ_apply = persistent_occupancy(P->bits, kModeApply + (P->fill ? 0 : P->mode), s);
         if (occ_apply < 1) return cudaGetLastError() != cudaSuccess ? RFI_ERR_CUDA : RFI_ERR_UNSUPPORTED;
         P->grid_apply = P->sm_count * occ_apply;  // clamped to the tile count with the grid
     }
@@ -146,8 +146,20 @@ rfi_status plan_alloc_workspace(rfi_plan_s *P) {
         P->nfblk = fblk.back();
         P->fill_grid = noise_fill_grid(P->sm_count);
     }
-    const size_t fb_b = al(sizeof(uint32_t) * fblk.size());
-    P->ws_bytes = seg_b + tile_b + (mom ? 3 : 2) * md_b + mc_b + pw_b + var_b + fb_b + ctr_b;
+    // one allocation, each array at the next 256-byte boundary
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += al(bytes);
+        return o;
+    };
+    const size_t o_ctr = take(ctr_b), o_seg = take(seg_b), o_tile = take(tile_b);
+    const size_t o_med = take(md_b), o_mad = take(md_b);
+    const size_t o_mom = mom ? take(md_b) : 0, o_mc = mom ? take(mc_b) : 0;
+    const size_t o_pw = P->power ? take(pw_b) : 0;
+    const size_t o_var = take(var_b);
+    const size_t o_fb = P->fill ? take(sizeof(uint32_t) * fblk.size()) : 0;
+    P->ws_bytes = off;
     if (P->ws) cudaFree(P->ws);
     P->ws = nullptr;
     if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
@@ -156,28 +168,28 @@ rfi_status plan_alloc_workspace(rfi_plan_s *P) {
         return RFI_ERR_OOM;
     }
     uint8_t *b = static_cast<uint8_t *>(P->ws);
-    P->d_ctr = reinterpret_cast<DevCounters *>(b);
-    P->d_segs = reinterpret_cast<Seg *>(b + ctr_b);
-    P->d_tiles = reinterpret_cast<Tile *>(b + ctr_b + seg_b);
-    P->d_med = reinterpret_cast<int32_t *>(b + ctr_b + seg_b + tile_b);
-    P->d_mad = reinterpret_cast<int32_t *>(b + ctr_b + seg_b + tile_b + md_b);
+    P->d_ctr = reinterpret_cast<DevCounters *>(b + o_ctr);
+    P->d_segs = reinterpret_cast<Seg *>(b + o_seg);
+    P->d_tiles = reinterpret_cast<Tile *>(b + o_tile);
+    P->d_med = reinterpret_cast<int32_t *>(b + o_med);
+    P->d_mad = reinterpret_cast<int32_t *>(b + o_mad);
     RFI_CUDA(cudaMemset(P->ws, 0, P->ws_bytes));
     RFI_CUDA(cudaMemcpy(P->d_tiles, P->tiles_host.data(), sizeof(Tile) * P->tiles_host.size(),
                         cudaMemcpyHostToDevice));
     if (mom) {
-        P->d_mom = reinterpret_cast<int32_t *>(b + ctr_b + seg_b + tile_b + 2 * md_b);
-        P->d_mchunks = reinterpret_cast<MomChunk *>(b + ctr_b + seg_b + tile_b + 3 * md_b);
+        P->d_mom = reinterpret_cast<int32_t *>(b + o_mom);
+        P->d_mchunks = reinterpret_cast<MomChunk *>(b + o_mc);
         RFI_CUDA(cudaMemcpy(P->d_mchunks, P->mchunks.data(), sizeof(MomChunk) * P->mchunks.size(),
                             cudaMemcpyHostToDevice));
     }
-    if (P->power) P->d_pow = reinterpret_cast<uint64_t *>(b + ctr_b + seg_b + tile_b + 2 * md_b + mc_b);
+    if (P->power) P->d_pow = reinterpret_cast<uint64_t *>(b + o_pw);
     if (!P->variants.empty()) {
-        P->d_var = reinterpret_cast<Variant *>(b + ctr_b + seg_b + tile_b + (mom ? 3 : 2) * md_b + mc_b + pw_b);
+        P->d_var = reinterpret_cast<Variant *>(b + o_var);
         RFI_CUDA(cudaMemcpy(P->d_var, P->variants.data(), sizeof(Variant) * P->variants.size(),
                             cudaMemcpyHostToDevice));
     }
     if (P->fill) {
-        P->d_fblk = reinterpret_cast<uint32_t *>(b + ctr_b + seg_b + tile_b + 2 * md_b + mc_b + pw_b + var_b);
+        P->d_fblk = reinterpret_cast<uint32_t *>(b + o_fb);
         RFI_CUDA(cudaMemcpy(P->d_fblk, fblk.data(), sizeof(uint32_t) * fblk.size(), cudaMemcpyHostToDevice));
     }
     P->segs_valid = false;
@@ -219,8 +231,11 @@ rfi_status plan_enqueue_batched(rfi_plan_s *P, cudaStream_t st) {
     RFI_CUDA(launch_mom(P->bits, P->d_mchunks, static_cast<int>(P->mchunks.size()), P->d_mad, P->d_mom, P->kmom,
                         st));
     RFI_CUDA(cudaMemsetAsync(&P->d_ctr->tile_counter, 0, sizeof(unsigned), st));
-    RFI_CUDA(launch_persistent(P->bits, kModeApply + P->mode, P->shape, P->grid_apply, P->d_segs + P->S, P->d_tiles,
-                               P->ntiles, p, &P->d_ctr->tile_counter, 0, st));
+    RFI_CUDA(launch_persistent(P->bits, kModeApply + (P->fill ? 0 : P->mode), P->shape, P->grid_apply, P->d_segs + P->S,
+                               P->d_tiles, P->ntiles, p, &P->d_ctr->tile_counter, 0, st));
+    // the apply segments hold each window's M and its MoM: the noise spread of Eq. 3
+    if (P->fill)
+        RFI_CUDA(launch_noise_fill(P->bits, P->d_segs + P->S, P->S, P->d_fblk, P->nfblk, p, P->fill_grid, st));
     return RFI_OK;
 }
 
@@ -414,7 +429,7 @@ static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_va
     bool short_segs = true;
     for (int i = 0; i < P->S; ++i) short_segs = short_segs && P->len[i] < (int64_t{1} << 31);
     P->fill = (P->flags & RFI_PLAN_NOISE_PASS) && P->mode == RFI_REPLACE_NOISE && !(P->flags & RFI_PLAN_PER_STREAM) &&
-              P->kmom < 2 && !P->power && P->ncopy == 0 && P->out_format == RFI_OUT_SAME && short_segs;
+              !P->power && P->ncopy == 0 && P->out_format == RFI_OUT_SAME && short_segs;
 
     rfi_status rs = RFI_OK;
     if (cudaGetDevice(&P->device) != cudaSuccess ||
@@ -726,7 +741,7 @@ rfi_status rfi_plan_get_info(rfi_plan_t P, rfi_plan_info *info) {
     info->shape.hist_copies = P->shape.hist_copies;
     info->shape.groups = P->shape.groups;
     info->sm_count = P->sm_count;
-    info->kernels_per_call = (P->flags & RFI_PLAN_PER_STREAM) ? P->S : (P->kmom >= 2 ? 3 : (P->fill ? 2 : 1));
+    info->kernels_per_call = (P->flags & RFI_PLAN_PER_STREAM) ? P->S : (P->kmom >= 2 ? 3 : 1) + (P->fill ? 1 : 0);
     return RFI_OK;
 }
 

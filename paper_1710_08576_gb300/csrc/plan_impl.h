@@ -113,7 +113,7 @@ std::vector<T> part_args(const rfi_plan_s *P, size_t k, T const *all) {
 // Kernel mode of a per-window MAD plan (the power-metered form when RFI_PLAN_POWER is set).
 inline int plan_kernel_mode(const rfi_plan_s *P) {
     const int fmt = P->out_format == RFI_OUT_F16 ? kModeF16 : (P->out_format == RFI_OUT_BF16 ? kModeBF16 : 0);
-    return P->ncopy > 0 ? kModeCopies : ((P->fill ? 0 : P->mode) | (P->power ? kModePower : 0) | fmt);
+    return P->ncopy > 0 ? kModeCopies : ((P->fill && P->kmom < 2 ? 0 : P->mode) | (P->power ? kModePower : 0) | fmt);
 }
 
 }  // namespace rfi

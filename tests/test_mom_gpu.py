@@ -39,7 +39,8 @@ def _gpu(rfi, xs, windows, bits, k, mode, kmom, const=0, seed=0, flags=0, sids=N
         st, totals = plan.stats(meds, mads)
         plan.stats_mom(moms)
         torch.cuda.synchronize()
-        assert plan.info().kernels_per_call == 3
+        noise_pass = bool(flags & rfi.RFI_PLAN_NOISE_PASS) and mode == 3
+        assert plan.info().kernels_per_call == (4 if noise_pass else 3)
         res = [dict(z=outs[i].cpu().numpy(), mask=masks[i].cpu().numpy().view(np.uint32),
                     counts=counts[i].cpu().numpy().view(np.uint32), median=meds[i].cpu().numpy(),
                     mad=mads[i].cpu().numpy(), mom=moms[i].cpu().numpy()) for i in range(len(xs))]
@@ -85,6 +86,20 @@ def test_mom_plan_matches_oracle(cuda, rfi, bits, windows, lens, kmom, mode):
         _check(got[i], ref, "stream %d" % i)
         flagged += int(ref["counts"].sum())
     assert totals.flagged == flagged
+
+
+@pytest.mark.parametrize("bits,windows,lens,kmom,mode", [c for c in CASES if c[4] == 3])
+def test_mom_noise_pass_matches_oracle(cuda, rfi, bits, windows, lens, kmom, mode):
+    """RFI_PLAN_NOISE_PASS: the apply pass replaces with 0 and a fourth kernel writes the noise
+    from each window's M and MoM; every output equals the oracle's."""
+    xs = _streams(bits, lens, 40 + kmom)
+    k = 3.0 if bits == 8 else 3.5
+    st, totals, got = _gpu(rfi, xs, windows, bits, k, mode, kmom, const=-2, seed=77,
+                           flags=rfi.RFI_PLAN_NOISE_PASS | rfi.RFI_PLAN_GRAPH)
+    assert st == rfi.RFI_OK and totals.device_status == rfi.RFI_OK
+    for i, x in enumerate(xs):
+        ref = oracle.excise_mom(x, windows[i], k, mode, kmom, const=-2, seed=77, stream_id=i, bits=bits, threads=8)
+        _check(got[i], ref, "stream %d" % i)
 
 
 def test_mom_graph_and_repeated_calls(cuda, rfi):
