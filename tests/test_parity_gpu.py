@@ -221,6 +221,10 @@ def test_host_pipeline(cuda, rfi, bits):
     assert st == 0
     assert_same(got, ref, "host pipeline %d-bit" % bits)
     assert totals.flagged == sum(int(r["counts"].sum()) for r in ref)
+    # a noise-pass plan keeps the noise in the chunk kernel on host buffers: the same bits
+    got, st, _, _ = gpu_run(rfi, xs, wins, bits, k, 3, seed=7, host=True, flags=rfi.RFI_PLAN_NOISE_PASS)
+    assert st == 0
+    assert_same(got, ref, "host pipeline, noise-pass plan, %d-bit" % bits)
 
 
 def test_repeated_calls_and_stream_ids(cuda, rfi):
