@@ -20,8 +20,6 @@ using rfi::Seg;
 using rfi::Shape;
 using rfi::Tile;
 
-rfi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RFI_OK : RFI_ERR_CUDA; }
-
 #define RFI_CUDA(call)                                   \
     do {                                                 \
         cudaError_t e_ = (call);                         \
@@ -710,7 +708,7 @@ rfi_status rfi_plan_get_info(rfi_plan_t P, rfi_plan_info *info) {
     if (!P->parts.empty()) {
         uint64_t most = 0;
         for (rfi_plan_s *c : P->parts) {
-            rfi_plan_info ci;
+            rfi_plan_info ci{};
             rfi_plan_get_info(c, &ci);
             info->workspace_bytes += ci.workspace_bytes;
             info->tiles += ci.tiles;
