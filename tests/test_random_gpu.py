@@ -1,0 +1,53 @@
+"""Seeded random sweep: the GPU path against the oracle, bit for bit, over random combinations of
+sample width, window lengths (1 to 70000, any residue mod 16 and 32), stream lengths (ragged
+tails), k, replacement mode, constant, noise seed, stream ids and plan form (batched, CUDA
+graph, digital noise as a second kernel, per-stream). Each case is small enough for the oracle
+to finish in well under a second; the draw is fixed by the case index."""
+import numpy as np
+import pytest
+
+import synth
+
+from .parity import assert_same, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+FORMS = [0, 0x4, 0x40, 0x40 | 0x4, 0x1]
+
+
+def _case(i):
+    rng = np.random.default_rng(1000 + i)
+    bits = int(rng.choice([8, 12]))
+    S = int(rng.integers(1, 5))
+    wins, lens = [], []
+    for _ in range(S):
+        W = int(rng.choice([int(rng.integers(1, 64)), int(rng.integers(64, 5000)), 4096, 16384,
+                            int(rng.integers(5000, 70000))]))
+        W = min(W, 65536)
+        nw = int(rng.integers(1, max(2, 300000 // W)))
+        n = max(1, nw * W - int(rng.integers(0, W)))
+        wins.append(W)
+        lens.append(n)
+    k = float(rng.choice([1.5, 2.0, 3.0, 3.5, 5.0, float(rng.uniform(0.5, 8.0))]))
+    mode = int(rng.integers(0, 4))
+    lo, hi = (-128, 127) if bits == 8 else (-2048, 2047)
+    const = int(rng.integers(lo - 50, hi + 50))  # saturated by the plan
+    seed = int(rng.integers(0, 2 ** 63))
+    sids = [int(v) for v in rng.integers(0, 2 ** 32, size=S)]
+    flags = int(FORMS[i % len(FORMS)])
+    sigma = float(rng.uniform(2.0, 30.0)) if bits == 8 else float(rng.uniform(20.0, 300.0))
+    p = synth.params(seed=int(rng.integers(0, 1 << 30)), sigma=sigma, burst_rate=float(rng.uniform(1e-4, 2e-2)),
+                     burst_len_max=int(rng.integers(1, 300)), bits=bits)
+    xs = [synth.fill(p, s, n) for s, n in enumerate(lens)]
+    return bits, wins, lens, k, mode, const, seed, sids, flags, xs
+
+
+@pytest.mark.parametrize("i", range(40))
+def test_random_case(cuda, rfi, i):
+    bits, wins, lens, k, mode, const, seed, sids, flags, xs = _case(i)
+    got, st, totals, _ = gpu_run(rfi, xs, wins, bits, k, mode, const, seed, flags=flags, stream_ids=sids)
+    assert st == 0
+    ref = oracle_run(xs, wins, bits, k, mode, const, seed, sids)
+    assert_same(got, ref, "case %d: bits %d W %s mode %d k %g flags %#x" % (i, bits, wins, mode, k, flags))
+    assert totals.flagged == sum(int(r["counts"].sum()) for r in ref)
+    assert totals.windows == sum(-(-n // w) for n, w in zip(lens, wins))
