@@ -51,3 +51,37 @@ def test_random_case(cuda, rfi, i):
     assert_same(got, ref, "case %d: bits %d W %s mode %d k %g flags %#x" % (i, bits, wins, mode, k, flags))
     assert totals.flagged == sum(int(r["counts"].sum()) for r in ref)
     assert totals.windows == sum(-(-n // w) for n, w in zip(lens, wins))
+
+
+def _mom_case(i):
+    rng = np.random.default_rng(5000 + i)
+    bits = int(rng.choice([8, 12]))
+    S = int(rng.integers(1, 4))
+    wins = [int(rng.choice([256, 512, 1000, 1024, 2048, 4096, int(rng.integers(16, 3000))])) for _ in range(S)]
+    lens = [max(1, int(rng.integers(1, 200)) * W - int(rng.integers(0, W))) for W in wins]
+    kmom = int(rng.choice([2, 3, 7, 64, 300, 5000]))
+    k = float(rng.choice([2.0, 3.0, 3.5, 5.0]))
+    mode = int(rng.integers(0, 4))
+    flags = int([0, 0x4, 0x40, 0x44][i % 4])
+    sigma = 16.0 if bits == 8 else 120.0
+    p = synth.params(seed=int(rng.integers(0, 1 << 30)), sigma=sigma, burst_rate=float(rng.uniform(1e-4, 5e-3)),
+                     burst_len_max=int(rng.integers(16, 5000)), bits=bits)
+    xs = [synth.fill(p, s, n) for s, n in enumerate(lens)]
+    return bits, wins, k, mode, kmom, flags, xs
+
+
+@pytest.mark.parametrize("i", range(16))
+def test_random_mom_case(cuda, rfi, i):
+    import oracle
+    from .test_mom_gpu import _check, _gpu
+    bits, wins, k, mode, kmom, flags, xs = _mom_case(i)
+    sids = [7 * s + 1 for s in range(len(xs))]
+    st, totals, got = _gpu(rfi, xs, wins, bits, k, mode, kmom, const=3, seed=1234 + i, flags=flags, sids=sids)
+    assert st == rfi.RFI_OK and totals.device_status == rfi.RFI_OK
+    flagged = 0
+    for s, x in enumerate(xs):
+        ref = oracle.excise_mom(x, wins[s], k, mode, kmom, const=3, seed=1234 + i, stream_id=sids[s], bits=bits,
+                                threads=8)
+        _check(got[s], ref, "case %d stream %d (W %d, kmom %d, mode %d, flags %#x)" % (i, s, wins[s], kmom, mode, flags))
+        flagged += int(ref["counts"].sum())
+    assert totals.flagged == flagged
