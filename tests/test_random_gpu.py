@@ -85,3 +85,36 @@ def test_random_mom_case(cuda, rfi, i):
         _check(got[s], ref, "case %d stream %d (W %d, kmom %d, mode %d, flags %#x)" % (i, s, wins[s], kmom, mode, flags))
         flagged += int(ref["counts"].sum())
     assert totals.flagged == flagged
+
+
+@pytest.mark.parametrize("i", range(12))
+def test_random_digital_copy_case(cuda, rfi, i):
+    from .test_copies_gpu import _check, _run, _streams
+    rng = np.random.default_rng(7000 + i)
+    bits = int(rng.choice([8, 12]))
+    S = int(rng.integers(1, 4))
+    wins = [int(rng.choice([16, 100, 1024, 4096, 16384, int(rng.integers(1, 20000))])) for _ in range(S)]
+    lens = [max(1, int(rng.integers(1, 30)) * W - int(rng.integers(0, W))) for W in wins]
+    nvar = int(rng.integers(1, 9))
+    variants = [(float(rng.choice([2.0, 3.0, 3.5, 5.0, float(rng.uniform(1.0, 6.0))])), int(rng.integers(0, 4)),
+                 int(rng.integers(-200, 200)), int(rng.integers(0, 2 ** 63))) for _ in range(nvar)]
+    xs = _streams(bits, lens, 70 + i)
+    st, totals, res, meds, mads = _run(rfi, xs, wins, bits, variants, flags=int([0, 0x4][i % 2]))
+    assert st == rfi.RFI_OK
+    assert totals.flagged == _check(xs, wins, bits, variants, res, meds, mads)
+
+
+@pytest.mark.parametrize("i", range(12))
+def test_random_output_format_case(cuda, rfi, i):
+    from .test_format_gpu import _check, _run, _streams
+    rng = np.random.default_rng(9000 + i)
+    bits = int(rng.choice([8, 12]))
+    fmt = rfi.RFI_OUT_F16 if bits == 12 or i % 2 else rfi.RFI_OUT_BF16
+    S = int(rng.integers(1, 4))
+    wins = [int(rng.choice([7, 64, 1000, 4096, 16384, 65536, int(rng.integers(1, 30000))])) for _ in range(S)]
+    lens = [max(1, int(rng.integers(1, 20)) * W - int(rng.integers(0, W))) for W in wins]
+    k = float(rng.choice([2.0, 3.0, 3.5, 5.0]))
+    mode = int(rng.integers(0, 4))
+    xs = _streams(bits, lens, 90 + i)
+    res = _run(rfi, xs, wins, bits, k, mode, fmt, flags=int([0, 0x4, 0x20][i % 3]), offset=2 * int(rng.integers(0, 4)))
+    _check(xs, wins, bits, k, mode, res)
