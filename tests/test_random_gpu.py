@@ -118,3 +118,24 @@ def test_random_output_format_case(cuda, rfi, i):
     xs = _streams(bits, lens, 90 + i)
     res = _run(rfi, xs, wins, bits, k, mode, fmt, flags=int([0, 0x4, 0x20][i % 3]), offset=2 * int(rng.integers(0, 4)))
     _check(xs, wins, bits, k, mode, res)
+
+
+@pytest.mark.parametrize("i", range(10))
+def test_random_power_case(cuda, rfi, i):
+    import oracle
+    from .test_power_gpu import _run, _streams
+    rng = np.random.default_rng(11000 + i)
+    bits = int(rng.choice([8, 12]))
+    S = int(rng.integers(1, 4))
+    wins = [int(rng.choice([1, 33, 512, 4096, 16384, 65536, int(rng.integers(1, 30000))])) for _ in range(S)]
+    lens = [max(1, int(rng.integers(1, 20)) * W - int(rng.integers(0, W))) for W in wins]
+    mode = int(rng.integers(0, 4))
+    k = float(rng.choice([2.0, 3.0, 5.0]))
+    flags = rfi.RFI_PLAN_POWER | int([0, 0x4, 0x20][i % 3])
+    xs = _streams(bits, lens, 110 + i)
+    z, m, pw = _run(rfi, xs, wins, bits, mode, flags, seed=70 + i, k=k)
+    for s, x in enumerate(xs):
+        ref = oracle.excise(x, wins[s], k, mode, const=2, seed=70 + i, stream_id=s, bits=bits, threads=8)
+        assert np.array_equal(z[s], ref["z"]), "case %d stream %d samples" % (i, s)
+        assert np.array_equal(pw[s][0::2], oracle.window_power(x, wins[s])), "case %d stream %d input power" % (i, s)
+        assert np.array_equal(pw[s][1::2], oracle.window_power(ref["z"], wins[s])), "case %d stream %d output" % (i, s)
