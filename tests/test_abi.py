@@ -62,6 +62,24 @@ int main(void) {
                                           rfi.RfiPlanInfo.shape.offset]
 
 
+def test_constants_match_header(tmp_path):
+    """Every RFI_* enum value and flag of the header equals the binding's constant of that name."""
+    text = open(HEADER).read()
+    names = sorted(set(re.findall(r"#define\s+(RFI_(?:PLAN|MAX)_\w+)\s", text)) |
+                   set(re.findall(r"\b(RFI_(?:OK|ERR_\w+|REPLACE_\w+|OUT_\w+))\s*=", text)))
+    assert "RFI_PLAN_NOISE_PASS" in names and "RFI_ERR_BUSY" in names and "RFI_OUT_BF16" in names
+    src = tmp_path / "consts.c"
+    src.write_text("#include <stdio.h>\n#include \"rfi.h\"\nint main(void) {\n" +
+                   "".join('  printf("%%s %%lld\\n", "%s", (long long)(%s));\n' % (n, n) for n in names) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "consts"
+    subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        name, value = line.split()
+        assert hasattr(rfi, name), name
+        assert getattr(rfi, name) == int(value), name
+
+
 @pytest.mark.parametrize("kw", [
     dict(bits=7), dict(bits=16), dict(stream_len=[0]), dict(window_len=[0]),
     dict(window_len=[65537]), dict(k=0.0), dict(k=-3.0), dict(k=float("nan")), dict(k=1e-7),
