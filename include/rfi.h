@@ -106,8 +106,8 @@ typedef enum { RFI_OUT_SAME = 0, RFI_OUT_F16 = 1, RFI_OUT_BF16 = 2 } rfi_out_for
                                      first rfi_excise with a NULL mask for some stream allocates a
                                      plan-owned mask array (ceil(W/32) words per window) that
                                      rfi_plan_destroy frees. Ignored with RFI_PLAN_PER_STREAM,
-                                     RFI_PLAN_POWER, fp16/bf16 output, by rfi_excise_host, and for
-                                     streams of 2^31 samples or more */
+                                     RFI_PLAN_POWER, fp16/bf16 output, by rfi_excise_host, and in
+                                     plans with a stream of 2^31 samples or more */
 #define RFI_PLAN_INJECT_TIMEOUT 0x100u /* test hook: CTA 0 waits on a barrier nothing arrives
                                           on (bounded by 1 ms), latching RFI_ERR_TIMEOUT */
 
