@@ -1090,6 +1090,29 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
     constexpr int OUTF = (MODE & kModeF16) ? 1 : ((MODE & kModeBF16) ? 2 : 0);
     constexpr int RMODE = MODE & 3;
     const int lane = tid & 31;
+    if (STATS) {
+        // Estimation only (the first pass of Eq. 3): M and D of the window. Nothing reads the
+        // stage after the histogram, so the tile's last window releases it there; the search
+        // warp writes M and D itself while the other warps go on to the next window. sg lives in
+        // the stage's descriptor, which the copy warp rewrites once the stage is released: its
+        // output pointers are taken first.
+        int32_t *const med = sg.med, *const mad = sg.mad;
+        if (stage_ok) phase_histogram<BITS, T, ROWB>(sm, w, tid, par);
+        if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
+        if (tid == 0 && release_bar) mbar_arrive(release_bar);
+        if (BITS == 8) phase_reduce_scan8<T, ROWB>(sm, tid, rs, w.n);
+        else phase_reduce_scan12<T>(sm, tid, w.n);
+        named_bar(sm.bar_id, T);
+        if (tid < 32) {
+            phase_search<BITS>(sm, w.n, lane, p.kq, p.cval);
+            if (lane == 0) {  // the lane that wrote the record
+                if (med) med[widx] = sm.ctl->rep.M;
+                if (mad) mad[widx] = sm.ctl->rep.D;
+                if (BITS == 12 && atomicExch(&sm.ctl->err[par], 0u)) atomicOr(p.status, kStatusSampleRange);
+            }
+        }
+        return true;
+    }
     if (!APPLY) {
         if (stage_ok) phase_histogram<BITS, T, ROWB>(sm, w, tid, par);
         if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
