@@ -450,6 +450,62 @@ __device__ __forceinline__ void phase_reduce_scan8(const Shm &sm, int tid, RowSu
     }
 }
 
+// 8-bit estimation pass: each thread's bins' counts for this window (the differences of its
+// running row sums) into the cumulative-count array, for one warp to scan.
+template <int T, int ROWB>
+__device__ __forceinline__ void phase_reduce8_counts(const Shm &sm, int tid, RowSums &rs) {
+    constexpr int TE = T < 256 ? T : 256;
+    constexpr int BPT = 256 / TE;
+    static_assert(BPT <= 2, "RowSums holds two rows");
+    const int lane = tid & 31;
+    if (tid < TE) {
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            const uint4 *row = reinterpret_cast<const uint4 *>(sm.hist + ((tid * BPT + i) ^ 128) * ROWB + sm.grp);
+            uint32_t s = 0;
+#pragma unroll
+            for (int q = 0; q < ROWB / 16; ++q) {
+                const uint4 a = row[(q + lane) & (ROWB / 16 - 1)];
+                s += a.x + a.y + a.z + a.w;
+            }
+            sm.cum[pad32(tid * BPT + i)] = s - rs.s[i];
+            rs.s[i] = s;
+        }
+    }
+}
+
+// One warp, after phase_reduce8_counts and a group barrier: the inclusive scan of the 256 counts
+// in place (8 consecutive bins per lane) and the median bin, the lowest whose cumulative count
+// reaches ceil(n/2), into the control block.
+__device__ __forceinline__ void phase_scan8_warp(const Shm &sm, int n, int lane) {
+    uint32_t *cum = sm.cum;
+    uint32_t c[8];
+    uint32_t run = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        run += cum[pad32(lane * 8 + j)];
+        c[j] = run;
+    }
+    uint32_t inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t excl = inc - run;
+    const uint32_t half = static_cast<uint32_t>((n + 1) >> 1);
+    int found = -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t v = c[j] + excl;
+        const uint32_t before = (j ? c[j - 1] : 0u) + excl;
+        cum[pad32(lane * 8 + j)] = v;
+        if (v >= half && before < half) found = lane * 8 + j;
+    }
+    if (found >= 0) sm.ctl->mb = found;
+    __syncwarp();
+}
+
 // 12-bit: fold the copies into padded totals (conflict-free strided pass), then scan
 // contiguous bins per thread.
 template <int T>
@@ -1100,10 +1156,13 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
         if (stage_ok) phase_histogram<BITS, T, ROWB>(sm, w, tid, par);
         if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
         if (tid == 0 && release_bar) mbar_arrive(release_bar);
-        if (BITS == 8) phase_reduce_scan8<T, ROWB>(sm, tid, rs, w.n);
+        // int8: the counts go to one warp, which scans them and searches while the other warps
+        // start the next window (one group barrier fewer than a block-wide scan)
+        if (BITS == 8) phase_reduce8_counts<T, ROWB>(sm, tid, rs);
         else phase_reduce_scan12<T>(sm, tid, w.n);
         named_bar(sm.bar_id, T);
         if (tid < 32) {
+            if (BITS == 8) phase_scan8_warp(sm, w.n, lane);
             phase_search<BITS>(sm, w.n, lane, p.kq, p.cval);
             if (lane == 0) {  // the lane that wrote the record
                 if (med) med[widx] = sm.ctl->rep.M;
