@@ -464,8 +464,8 @@ __device__ __forceinline__ void phase_reduce8_counts(const Shm &sm, int tid, Row
             const uint4 *row = reinterpret_cast<const uint4 *>(sm.hist + ((tid * BPT + i) ^ 128) * ROWB + sm.grp);
             uint32_t s = 0;
 #pragma unroll
-            for (int q = 0; q < ROWB / 16; ++q) {
-                const uint4 a = row[(q + lane) & (ROWB / 16 - 1)];
+            for (int q = 0; q < 8; ++q) {  // this group's 32 lane counters (128 bytes of the row)
+                const uint4 a = row[(q + lane) & 7];
                 s += a.x + a.y + a.z + a.w;
             }
             sm.cum[pad32(tid * BPT + i)] = s - rs.s[i];
@@ -1175,10 +1175,13 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
     if (!APPLY) {
         if (stage_ok) phase_histogram<BITS, T, ROWB>(sm, w, tid, par);
         if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
-        if (BITS == 8) phase_reduce_scan8<T, ROWB>(sm, tid, rs, w.n);
+        if (BITS == 8) phase_reduce8_counts<T, ROWB>(sm, tid, rs);
         else phase_reduce_scan12<T>(sm, tid, w.n);
         named_bar(sm.bar_id, T);
-        if (tid < 32) phase_search<BITS>(sm, w.n, lane, p.kq, p.cval);
+        if (tid < 32) {
+            if (BITS == 8) phase_scan8_warp(sm, w.n, lane);
+            phase_search<BITS>(sm, w.n, lane, p.kq, p.cval);
+        }
     } else {
         // every thread has read the previous window's values before this barrier
         if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
