@@ -88,25 +88,37 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm, mx, reasons, power = [], None, set(), []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
-            f = [v.strip() for v in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-                power.append(float(f[3]))
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        loaded = [s for s in sm if mx and s > 0.5 * mx] or sm
-        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm),
-                "power_w_max": max(power) if power else None}
+        return summarize_clocks(self.lines)
+
+
+def summarize_clocks(lines):
+    """Summary of `nvidia-smi --query-gpu=<ClockSampler.FIELDS> --format=csv,noheader,nounits`
+    lines: the median SM clock over the samples under load (above half the maximum clock, or all
+    of them if none is), the maximum clock, the throttle reasons seen active, the sample count
+    and the highest power draw. Lines that do not parse are skipped."""
+    sm, mx, reasons, power = [], None, set(), []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        f = [v.strip() for v in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            clk, cmax = float(f[1]), float(f[2])
+        except ValueError:
+            continue
+        sm.append(clk)
+        mx = cmax
+        try:
+            power.append(float(f[3]))
+        except ValueError:  # "[N/A]" on parts that do not report it
+            pass
+        for n, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    loaded = [c for c in sm if mx and c > 0.5 * mx] or sm
+    return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": mx,
+            "reasons": sorted(reasons), "samples": len(sm),
+            "power_w_max": max(power) if power else None}
 
 
 # ------------------------------------------------------------------ helpers

@@ -1,0 +1,44 @@
+"""Host-side logic of bench.py that decides whether a run is kept: the summary of the GPU clocks
+sampled during the timed region (median SM clock under load, throttle reasons, power)."""
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import bench  # noqa: E402
+
+
+def _line(sm, mx=2070, power=800.0, active="0x0", hw="Not Active", hwt="Not Active", swt="Not Active",
+          cap="Not Active"):
+    return "0, %s, %s, %s, %s, %s, %s, %s, %s" % (sm, mx, power, active, hw, hwt, swt, cap)
+
+
+def test_median_under_load_ignores_idle_samples():
+    lines = [_line(345), _line(2070), _line(2055), _line(2070), _line(400)]
+    c = bench.summarize_clocks(lines)
+    assert c["sm_mhz"] == 2070 and c["sm_max_mhz"] == 2070 and c["samples"] == 5
+    assert c["reasons"] == [] and c["power_w_max"] == 800.0
+
+
+def test_all_idle_samples_still_give_a_median():
+    c = bench.summarize_clocks([_line(300), _line(330), _line(360)])
+    assert c["sm_mhz"] == 330
+
+
+def test_throttle_reasons_are_collected():
+    lines = [_line(2070), _line(1800, hwt="Active"), _line(1900, cap="Active"), _line(1950, swt="active")]
+    c = bench.summarize_clocks(lines)
+    assert c["reasons"] == ["hw_thermal_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    assert c["sm_mhz"] == 1925
+
+
+def test_unparsable_lines_and_missing_power_are_tolerated():
+    lines = ["", "garbage", _line("[N/A]"), _line(2070, power="[N/A]"), _line(2040, power=950.5),
+             "0, 1, 2"]
+    c = bench.summarize_clocks(lines)
+    assert c["samples"] == 2 and c["sm_mhz"] == 2055 and c["power_w_max"] == 950.5
+
+
+def test_no_samples():
+    c = bench.summarize_clocks([])
+    assert c["sm_mhz"] is None and c["samples"] == 0 and c["power_w_max"] is None
