@@ -1,5 +1,6 @@
 """Host-side logic of bench.py that decides whether a run is kept: the summary of the GPU clocks
-sampled during the timed region (median SM clock under load, throttle reasons, power)."""
+sampled during the timed region (median SM clock under load, throttle reasons, power), the
+number of the committed ncu summary it may report, and the HBM peak it divides by."""
 import os
 import sys
 
@@ -42,3 +43,21 @@ def test_unparsable_lines_and_missing_power_are_tolerated():
 def test_no_samples():
     c = bench.summarize_clocks([])
     assert c["sm_mhz"] is None and c["samples"] == 0 and c["power_w_max"] is None
+
+
+def test_profile_with_another_hash_gives_no_traffic(tmp_path, monkeypatch):
+    p = tmp_path / "profile.md"
+    p.write_text("source_hash: 0123456789abcdef\ntraffic_bytes_per_launch: 123\n")
+    monkeypatch.setattr(bench, "PROFILE", str(p))
+    assert bench.profiled_traffic() == (None, "kernel changed since the profile")
+    p.write_text("no figures here\n")
+    assert bench.profiled_traffic() == (None, "profile without traffic")
+    monkeypatch.setattr(bench, "PROFILE", str(tmp_path / "missing.md"))
+    assert bench.profiled_traffic() == (None, "no profile")
+
+
+def test_peak_falls_back_without_the_measured_file(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6790.7}')
+    assert bench.measured_peaks() == (6790.7, "measured")
