@@ -410,46 +410,6 @@ __device__ __forceinline__ uint32_t block_offsets(const Shm &sm, uint32_t run, i
     return pre + inc - run;
 }
 
-// 8-bit: thread t owns logical bins [t*BPT, (t+1)*BPT); logical bin v is lane-striped row v^128.
-// Sums its rows (the difference from the previous sum is this window's count), scans, writes
-// the inclusive cumulative counts, and the thread whose bin holds the ceil(n/2)-th sample
-// records it as the median bin.
-template <int T, int ROWB>
-__device__ __forceinline__ void phase_reduce_scan8(const Shm &sm, int tid, RowSums &rs, int n) {
-    constexpr int TE = T < 256 ? T : 256;
-    constexpr int BPT = 256 / TE;
-    static_assert(BPT <= 2, "RowSums holds two rows");
-    const int lane = tid & 31;
-    uint32_t v[BPT], h[BPT];
-    uint32_t run = 0;
-    if (tid < TE) {
-#pragma unroll
-        for (int i = 0; i < BPT; ++i) {
-            const uint4 *row = reinterpret_cast<const uint4 *>(sm.hist + ((tid * BPT + i) ^ 128) * ROWB + sm.grp);
-            uint32_t s = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const uint4 a = row[(q + lane) & 7];
-                s += a.x + a.y + a.z + a.w;
-            }
-            h[i] = s - rs.s[i];
-            rs.s[i] = s;
-            run += h[i];
-            v[i] = run;
-        }
-    }
-    const uint32_t excl = block_offsets<T>(sm, run, tid);
-    if (tid < TE) {
-        const uint32_t half = static_cast<uint32_t>((n + 1) >> 1);
-#pragma unroll
-        for (int i = 0; i < BPT; ++i) {
-            const uint32_t c = v[i] + excl;
-            sm.cum[pad32(tid * BPT + i)] = c;
-            if (c >= half && c - h[i] < half) sm.ctl->mb = tid * BPT + i;
-        }
-    }
-}
-
 // 8-bit estimation pass: each thread's bins' counts for this window (the differences of its
 // running row sums) into the cumulative-count array, for one warp to scan.
 template <int T, int ROWB>
