@@ -40,7 +40,12 @@ def _gpu(rfi, xs, windows, bits, k, mode, kmom, const=0, seed=0, flags=0, sids=N
         plan.stats_mom(moms)
         torch.cuda.synchronize()
         noise_pass = bool(flags & rfi.RFI_PLAN_NOISE_PASS) and mode == 3
-        assert plan.info().kernels_per_call == (4 if noise_pass else 3)
+        # windows that span more than one stage class (at most 16 KiB, at most 32 KiB, larger; by
+        # the window's bytes, or the stream's when it is shorter) make one internal plan per class
+        esz = 1 if bits == 8 else 2
+        parts = len({0 if b <= 16384 else (1 if b <= 32768 else 2)
+                     for b in (min(W, x.size) * esz for W, x in zip(windows, xs))})
+        assert plan.info().kernels_per_call == parts * (4 if noise_pass else 3)
         res = [dict(z=outs[i].cpu().numpy(), mask=masks[i].cpu().numpy().view(np.uint32),
                     counts=counts[i].cpu().numpy().view(np.uint32), median=meds[i].cpu().numpy(),
                     mad=mads[i].cpu().numpy(), mom=moms[i].cpu().numpy()) for i in range(len(xs))]
@@ -100,6 +105,30 @@ def test_mom_noise_pass_matches_oracle(cuda, rfi, bits, windows, lens, kmom, mod
     for i, x in enumerate(xs):
         ref = oracle.excise_mom(x, windows[i], k, mode, kmom, const=-2, seed=77, stream_id=i, bits=bits, threads=8)
         _check(got[i], ref, "stream %d" % i)
+
+
+@pytest.mark.parametrize("bits", [8, 12])
+def test_mom_many_streams(cuda, rfi, bits):
+    """120 streams of mixed window lengths (16 to 16384 samples) and lengths (one sample to a few
+    hundred windows): the estimation pass, the sliding median over each stream's own MADs and the
+    apply pass (and the noise pass) keep every stream's windows apart."""
+    rng = np.random.default_rng(6060 + bits)
+    S = 120
+    wins = [int(rng.choice([16, 100, 256, 1000, 1024, 4096, 16384])) for _ in range(S)]
+    lens = [int(rng.integers(1, min(300 * W, 1 << 18))) for W in wins]
+    sids = [int(v) for v in rng.integers(0, 2 ** 32, size=S)]
+    xs = _streams(bits, lens, 60 + bits)
+    k = 3.0 if bits == 8 else 3.5
+    for kmom, mode, flags in ((7, 3, rfi.RFI_PLAN_GRAPH), (64, 3, rfi.RFI_PLAN_NOISE_PASS), (2, 2, 0)):
+        st, totals, got = _gpu(rfi, xs, wins, bits, k, mode, kmom, const=4, seed=21, flags=flags, sids=sids)
+        assert st == rfi.RFI_OK and totals.device_status == rfi.RFI_OK
+        flagged = 0
+        for i, x in enumerate(xs):
+            ref = oracle.excise_mom(x, wins[i], k, mode, kmom, const=4, seed=21, stream_id=sids[i], bits=bits,
+                                    threads=8)
+            _check(got[i], ref, "stream %d (W %d, kmom %d, flags %#x)" % (i, wins[i], kmom, flags))
+            flagged += int(ref["counts"].sum())
+        assert totals.flagged == flagged
 
 
 def test_mom_graph_and_repeated_calls(cuda, rfi):

@@ -164,6 +164,31 @@ def test_noise_pass_without_caller_masks(cuda, rfi, bits):
         plan.close()
 
 
+@pytest.mark.parametrize("bits", [8, 12])
+def test_many_streams_of_mixed_lengths_and_windows(cuda, rfi, bits):
+    """300 streams, lengths from 1 sample to a few windows, windows from 1 to 65536 samples: the
+    work list, the segment tables, the split by window class and the noise pass's per-segment
+    mask blocks all span hundreds of segments. Every form against one oracle run per mode."""
+    rng = np.random.default_rng(4242 + bits)
+    S = 300
+    wins = [min(65536, int(rng.choice([1, 7, 32, 100, 1024, 4096, 16384, 65536, int(rng.integers(1, 70000))])))
+            for _ in range(S)]
+    lens = [int(rng.integers(1, 3 * min(W, 20000) + 2)) for W in wins]
+    sids = [int(v) for v in rng.integers(0, 2 ** 32, size=S)]
+    p = synth.params(seed=77 + bits, sigma=16.0 if bits == 8 else 120.0, burst_rate=5e-3, burst_len_max=200,
+                     bits=bits)
+    xs = [synth.fill(p, s, n) for s, n in enumerate(lens)]
+    for mode in (2, 3):
+        ref = oracle_run(xs, wins, bits, 3.0, mode, 0, 11, sids)
+        flagged = sum(int(r["counts"].sum()) for r in ref)
+        for form, flags in FORMS.items():
+            got, st, totals, _ = gpu_run(rfi, xs, wins, bits, 3.0, mode, 0, 11, flags=flags, stream_ids=sids)
+            assert st == 0
+            assert_same(got, ref, "%d streams, bits %d mode %d form %s" % (S, bits, mode, form))
+            assert totals.flagged == flagged
+            assert totals.windows == sum(-(-n // W) for n, W in zip(lens, wins))
+
+
 def test_degenerate_windows(cuda, rfi):
     W = 4096
     a = np.zeros(W, np.int8)                         # constant: D = 0
