@@ -49,17 +49,23 @@ int main(void) {
          sizeof(rfi_totals), sizeof(rfi_plan_info), offsetof(rfi_plan_desc, shape));
   printf("%zu %zu %zu\n", offsetof(rfi_plan_desc, k), offsetof(rfi_plan_desc, seed),
          offsetof(rfi_plan_info, shape));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(rfi_variant), offsetof(rfi_variant, seed),
+         offsetof(rfi_plan_desc, mom_windows), offsetof(rfi_plan_desc, out_format),
+         offsetof(rfi_plan_info, kernels_per_call));
   return 0;
 }''')
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
-    a, b = subprocess.check_output([str(exe)], text=True).splitlines()
+    a, b, c = subprocess.check_output([str(exe)], text=True).splitlines()
     C = ctypes
     assert [int(v) for v in a.split()] == [C.sizeof(rfi.RfiLaunchShape), C.sizeof(rfi.RfiPlanDesc),
                                           C.sizeof(rfi.RfiTotals), C.sizeof(rfi.RfiPlanInfo),
                                           rfi.RfiPlanDesc.shape.offset]
     assert [int(v) for v in b.split()] == [rfi.RfiPlanDesc.k.offset, rfi.RfiPlanDesc.seed.offset,
                                           rfi.RfiPlanInfo.shape.offset]
+    assert [int(v) for v in c.split()] == [C.sizeof(rfi.RfiVariant), rfi.RfiVariant.seed.offset,
+                                          rfi.RfiPlanDesc.mom_windows.offset, rfi.RfiPlanDesc.out_format.offset,
+                                          rfi.RfiPlanInfo.kernels_per_call.offset]
 
 
 def test_constants_match_header(tmp_path):
