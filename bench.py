@@ -736,7 +736,7 @@ def run_serve(args):
     return 0
 
 
-def main():
+def make_parser():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
@@ -755,7 +755,12 @@ def main():
     ap.add_argument("--workload", choices=["gwb60", "twelve60", "uneven60", "serve60"], default="gwb60")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--feed", choices=["device", "host"], default="device")
-    args = ap.parse_args()
+    return ap
+
+
+def main(argv=None):
+    ap = make_parser()
+    args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":

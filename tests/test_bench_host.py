@@ -61,3 +61,35 @@ def test_peak_falls_back_without_the_measured_file(tmp_path, monkeypatch):
     assert bench.measured_peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6790.7}')
     assert bench.measured_peaks() == (6790.7, "measured")
+
+
+def _profile_commands():
+    """Every shell command in the fenced blocks of the committed ncu summaries, with backslash
+    continuations joined."""
+    root = os.path.join(os.path.dirname(bench.__file__), "profiles")
+    cmds = []
+    for name in sorted(os.listdir(root)):
+        if not name.endswith(".md"):
+            continue
+        text = open(os.path.join(root, name)).read()
+        for block in text.split("```")[1::2]:
+            joined = block.replace("\\\n", " ")
+            cmds += [(name, c.strip()) for c in joined.splitlines() if c.strip()]
+    return cmds
+
+
+def test_profile_commands_run_committed_files_with_valid_options():
+    import shlex
+    cmds = _profile_commands()
+    assert cmds
+    benched = 0
+    for name, c in cmds:
+        if c.startswith("ncu "):
+            assert "--clock-control none" in c, (name, c)
+        if "python bench.py" in c:
+            args = bench.make_parser().parse_args(shlex.split(c.split("python bench.py", 1)[1]))
+            assert args.warmup >= 3, (name, c)
+            benched += 1
+        assert "_work/" not in c, (name, c)
+    assert benched >= len([n for n in os.listdir(os.path.join(os.path.dirname(bench.__file__), "profiles"))
+                           if n.endswith(".md")])
