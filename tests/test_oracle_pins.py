@@ -372,3 +372,109 @@ def test_noise_mode_uses_absolute_index_and_saturates():
             assert int(r2["z"][i]) == max(-128, min(127, raw))
             clamped += raw > 127
     assert clamped > 0
+
+
+# ---------------------------------------------------------------- digital noise: worked values
+def load_noise_golden():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "noise.txt")):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            rows.append(dict(name=f[0], seed=int(f[1], 0), idx=int(f[2]), stream=int(f[3]), M=int(f[4]),
+                             D=int(f[5]), bits=int(f[6]), r=[int(v, 0) for v in f[7:11]], sum_u=int(f[11]),
+                             S2=int(f[12]), num=int(f[13]), q=int(f[14]), rem=int(f[15]), off=int(f[16]),
+                             value=int(f[17])))
+    return rows
+
+
+NOISE_DEN = 107020 * 65536
+
+
+@pytest.mark.parametrize("g", load_noise_golden(), ids=lambda g: g["name"])
+def test_noise_golden(g):
+    """Each row's worked steps hold together, its Philox words are cuRAND's (when the library is
+    present) and the oracle's, and the oracle's replacement value is the worked value."""
+    key = (g["seed"] & 0xFFFFFFFF, g["seed"] >> 32)
+    ctr = (g["idx"] & 0xFFFFFFFF, g["idx"] >> 32, g["stream"], 0)
+    assert oracle.philox4x32_10(ctr, key) == g["r"]
+    cr = _curand()
+    if cr is not None:
+        gen = ctypes.c_void_p()
+        assert cr.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0
+        try:
+            assert cr.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_uint64(g["seed"])) == 0
+            block = 65536 * ctr[0] + g["stream"] + (65536 << 32) * ctr[1]
+            assert cr.curandSetGeneratorOffset(gen, ctypes.c_uint64(4 * block)) == 0
+            buf = (ctypes.c_uint32 * 4)()
+            assert cr.curandGenerate(gen, buf, ctypes.c_size_t(4)) == 0
+            assert list(buf) == g["r"]
+        finally:
+            cr.curandDestroyGenerator(gen)
+    # the row's own arithmetic (steps 2-5 of the fixture header)
+    assert sum((w & 0xFFFF) + (w >> 16) for w in g["r"]) == g["sum_u"]
+    assert g["S2"] == 2 * g["sum_u"] - 8 * 65535
+    assert g["num"] == g["S2"] * 97164 * g["D"]
+    assert abs(g["num"]) == g["q"] * NOISE_DEN + g["rem"] and 0 <= g["rem"] < NOISE_DEN
+    assert abs(g["off"]) == g["q"] + (1 if 2 * g["rem"] >= NOISE_DEN else 0)
+    lo, hi = (-128, 127) if g["bits"] == 8 else (-2048, 2047)
+    assert g["value"] == max(lo, min(hi, g["M"] + g["off"]))
+    # the oracle
+    assert oracle.noise_value(g["M"], g["D"], g["seed"], g["stream"], g["idx"], g["bits"]) == g["value"]
+
+
+def _count_le(t):
+    """#{(h_1..h_8) in [0, 65535]^8 : sum <= t}, by inclusion-exclusion over the halves that
+    exceed their range (the distribution function of a sum of uniform 16-bit integers)."""
+    if t < 0:
+        return 0
+    return sum((-1) ** j * math.comb(8, j) * math.comb(t - 65536 * j + 8, 8)
+               for j in range(9) if t - 65536 * j >= 0)
+
+
+def _exact_noise_pmf(D):
+    """P(off = v) for a sample's noise offset at dispersion D, exactly, with S2 = 2*sum_u - 524280
+    (sum_u a sum of eight uniform 16-bit halves) and off the value S2*97164*D/(107020*2^16)
+    rounded half away from zero. Computed by locating where the offset steps in sum_u."""
+    from fractions import Fraction
+
+    def off(s):
+        x = Fraction((2 * s - 524280) * 97164 * D, NOISE_DEN)
+        m = abs(x)
+        r = math.floor(m + Fraction(1, 2))
+        return r if x >= 0 else -r
+
+    lo_v, hi_v = off(0), off(524280)
+
+    def first_s(v):  # smallest s with off(s) >= v (off is nondecreasing in s)
+        a, b = 0, 524281
+        while a < b:
+            mid = (a + b) // 2
+            if off(mid) >= v:
+                b = mid
+            else:
+                a = mid + 1
+        return a
+
+    total = 65536 ** 8
+    pmf = {}
+    for v in range(lo_v, hi_v + 1):
+        pmf[v] = Fraction(_count_le(first_s(v + 1) - 1) - _count_le(first_s(v) - 1), total)
+    assert sum(pmf.values()) == 1
+    return pmf
+
+
+@pytest.mark.parametrize("D,N", [(1, 400000), (2, 200000), (3, 200000)])
+def test_noise_exact_distribution_at_small_dispersion(D, N):
+    """At D = 1..3 the noise offset takes a handful of values whose probabilities follow exactly
+    from the Philox halves being uniform; the oracle's frequencies over N consecutive indices
+    must match each within 5 binomial sd. Rounding down instead of to nearest moves P(0) from
+    about 0.26 to about 0.5 at D = 1."""
+    pmf = _exact_noise_pmf(D)
+    vals = np.fromiter((oracle.noise_value(0, D, 0xD1CE, 3, i, 12) for i in range(N)), np.int64, N)
+    seen = {int(v): int(c) for v, c in zip(*np.unique(vals, return_counts=True))}
+    assert set(seen) <= set(pmf)
+    for v, p in pmf.items():
+        p = float(p)
+        assert abs(seen.get(v, 0) - N * p) <= 5 * math.sqrt(N * p * (1 - p)) + 1, (D, v, seen.get(v, 0), N * p)
+    # mean zero to within 0.01 LSB here; a one-sided rounding bias of 0.5 LSB would fail
+    assert abs(vals.mean()) < 5 * vals.std() / math.sqrt(N)
