@@ -13,7 +13,11 @@ Arms and keys of the JSON line:
               copies inside the timed region
   roofline    algorithmic bytes per launch / mean launch time of the persistent kernel, against
               the measured HBM copy bandwidth
-  cpu_baseline  the CPU oracle on a bounded sample of the same workload (host cores)
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload (host cores), with its
+              single-core throughput beside it
+  uneven60, twelve60, serve60   the other configurations at N = 1, each in its own sub-object:
+              batched throughput and HBM fraction (uneven60, twelve60), and a short serving run
+              (chunk latency percentiles, RTF)
 --impl reference times the CPU oracle alone on the same workload (bounded sample per step).
 """
 from __future__ import annotations
@@ -177,6 +181,106 @@ def cpu_oracle_sample(xs, variants, windows_per_stream, W, bits=8):
     return n, time.perf_counter() - t0, threads
 
 
+def cpu_oracle_single_core(xs, variants, windows_per_stream, W, bits=8, streams=8):
+    """The oracle on one host thread: the first windows_per_stream windows of the first `streams`
+    streams for every variant; returns (samples, seconds)."""
+    import oracle
+    Ws = list(W) if isinstance(W, (list, tuple)) else [W] * len(xs)
+    n, t0 = 0, time.perf_counter()
+    for v in variants:
+        for i, x in enumerate(xs[:streams]):
+            part = x[: windows_per_stream * Ws[i]]
+            oracle.excise(part, Ws[i], v.k, v.mode, const=v.const, seed=v.seed, stream_id=i, bits=bits,
+                          threads=1, want=("z", "mask", "counts"))
+            n += part.size
+    return n, time.perf_counter() - t0
+
+
+def choose_noise_form(rfi, plan, make_alt, call_ms):
+    """The faster digital-noise form of a noise plan on the benchmark's own data: the plan as
+    given (noise in the excision kernel) or its RFI_PLAN_NOISE_PASS twin. Returns the plan kept
+    and a record of both times."""
+    alt = make_alt()
+    one, two = call_ms(plan), call_ms(alt)
+    if two < one:
+        plan.close()
+        plan = alt
+    else:
+        alt.close()
+    return plan, {"form": "second kernel" if two < one else "in the excision kernel",
+                  "ms_in_kernel": round(one, 4), "ms_second_kernel": round(two, 4)}
+
+
+def workload_arm(name, steps, warmup, dev, stream, peak, group, sids_of):
+    """Batched excision of one further workload (uneven60 or twelve60) on this GPU: the benchmark's
+    plan form (CUDA graph, autotuned shape, the faster noise form), `steps` calls timed with CUDA
+    events on the launching stream. Returns the sub-object of the JSON line."""
+    import torch
+
+    import paper_1710_08576_gb300 as rfi
+    import synth
+    from synth import workloads
+    w = workloads.twelve60() if name == "twelve60" else workloads.uneven60()
+    bits, esz = w.bits, (1 if w.bits == 8 else 2)
+    S = len(w.streams)
+    sids = sids_of(S)
+    Ws = [s_.window for s_ in w.streams]
+    t_gen = time.perf_counter()
+    xs = [synth.fill(s_.feed, sid, s_.length) for s_, sid in zip(w.streams, sids)]
+    t_gen = time.perf_counter() - t_gen
+    lens = [x.size for x in xs]
+    dev_in = [torch.from_numpy(x).to(dev) for x in xs]
+    out = [torch.empty_like(t) for t in dev_in]
+    nwin = [-(-n // Ws[i]) for i, n in enumerate(lens)]
+    masks = [torch.empty(nw * ((Ws[i] + 31) // 32), dtype=torch.int32, device=dev) for i, nw in enumerate(nwin)]
+    counts = [torch.empty(nw, dtype=torch.int32, device=dev) for nw in nwin]
+    v = w.variants[0]
+    pflags = rfi.RFI_PLAN_GRAPH | rfi.RFI_PLAN_AUTOTUNE
+
+    def call_ms(plan, calls=3):
+        with torch.cuda.stream(stream):
+            plan.excise(dev_in, out, masks, counts, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(calls):
+                plan.excise(dev_in, out, masks, counts, stream)
+            e1.record(stream)
+            stream.synchronize()
+        return group.max(e0.elapsed_time(e1)) / calls
+
+    plan = rfi.Plan(bits, lens, Ws, v.k, v.mode, v.const, v.seed, pflags, sids)
+    plan, form = choose_noise_form(
+        rfi, plan, lambda: rfi.Plan(bits, lens, Ws, v.k, v.mode, v.const, v.seed, pflags | rfi.RFI_PLAN_NOISE_PASS,
+                                    sids), call_ms)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            plan.excise(dev_in, out, masks, counts, stream)
+        stream.synchronize()
+        group.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            a.record(stream)
+            plan.excise(dev_in, out, masks, counts, stream)
+            b.record(stream)
+        stream.synchronize()
+    group.barrier()
+    st, _ = plan.stats(stream=stream)
+    if st != 0:
+        raise RuntimeError("%s device status %s" % (name, rfi.rfi_status_string(st)))
+    info = plan.info()
+    plan.close()
+    mean_ms = group.max(statistics.mean(a.elapsed_time(b) for a, b in ev))
+    samples = sum(lens)
+    alg = samples * (2 * esz + 1 / 8) + sum(nwin) * 12
+    return {"value": group.sum(samples) / (mean_ms * 1e-3) / 1e9, "unit": UNIT,
+            "workload": workload_desc(S, 0, name), "samples": samples, "windows": sum(nwin),
+            "calls": steps, "ms_per_call": mean_ms, "achieved_gbs": alg / (mean_ms * 1e-3) / 1e9,
+            "frac": alg / (mean_ms * 1e-3) / 1e9 / peak,
+            "bytes_rule": "per sample 1 read + 1 write (%d B each) + 1/8 mask; per window 4 count + 8 M/D" % esz,
+            "noise_form": form, "launches_per_call": info.kernels_per_call,
+            "dtype": "int8" if bits == 8 else "int16", "feed_gen_s": round(t_gen, 2)}
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args):
     rank, _, world = env_rank()
@@ -276,15 +380,9 @@ def run_ours(args):
     for j, v in enumerate(w.variants):
         if v.mode != workloads.NOISE:
             continue
-        alt = rfi.Plan(bits, lens, Ws, v.k, v.mode, v.const, v.seed, pflags | rfi.RFI_PLAN_NOISE_PASS, sids)
-        one, two = plan_call_ms(batched[j]), plan_call_ms(alt)
-        if two < one:
-            batched[j].close()
-            batched[j] = alt
-        else:
-            alt.close()
-        noise_forms[v.name] = {"form": "second kernel" if two < one else "in the excision kernel",
-                               "ms_in_kernel": round(one, 4), "ms_second_kernel": round(two, 4)}
+        batched[j], noise_forms[v.name] = choose_noise_form(
+            rfi, batched[j], lambda v=v: rfi.Plan(bits, lens, Ws, v.k, v.mode, v.const, v.seed,
+                                                  pflags | rfi.RFI_PLAN_NOISE_PASS, sids), plan_call_ms)
     info = batched[0].info()
 
     def timed(plans, steps, warmup, per_call_events=True):
@@ -501,9 +599,31 @@ def run_ours(args):
                "sample": "first %d windows of each of the %d streams, all 8 variants (%d samples, %.1f s)"
                          % (args.cpu_windows, S, n, t)}
 
+    if cpu is not None:
+        n1, t1 = cpu_oracle_single_core(xs, w.variants, args.cpu_windows // 4, Ws, bits)
+        cpu["single_core"] = {"value": n1 / t1 / 1e9, "unit": UNIT, "cores": 1,
+                              "sample": "first %d windows of each of the first 8 streams, all %d variants "
+                                        "(%d samples, %.1f s)" % (args.cpu_windows // 4, len(w.variants), n1, t1)}
+
     launches_per_step = sum(p.info().kernels_per_call for p in batched)
     for p in batched + per_stream:
         p.close()
+
+    # the other configurations, at N = 1: uneven60 and twelve60 batched, and a short serving run
+    subs = {}
+    if args.workload == "gwb60" and world == 1 and not args.no_subs:
+        del dev_in, out, masks, counts
+        torch.cuda.empty_cache()
+        for name in ("uneven60", "twelve60"):
+            subs[name] = workload_arm(name, args.sub_steps, 3, dev, stream, peak, group,
+                                      lambda n: rdist.stream_ids(rank, n))
+            torch.cuda.empty_cache()
+        sv = run_serve(args, seconds=args.sub_serve_seconds, group=group, emit=False)
+        subs["serve60"] = {"value": sv["value"], "unit": UNIT, "workload": sv["config"]["workload"],
+                           **{k: sv["serve"][k] for k in ("stream_seconds", "wall_seconds", "rtf", "chunks",
+                                                          "requests", "push_stalls", "request_stalls",
+                                                          "chunk_latency_us", "chunk_device_latency_us",
+                                                          "request_latency_us", "gsps_in_passes")}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -529,6 +649,10 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "traffic_source": traffic_src,
+                         "traffic_note": "ncu DRAM bytes of a 16 x 2^24-sample capture, scaled by the units "
+                                         "processed (15x); reads scale exactly, but the capture's last output "
+                                         "lines were still dirty in L2 (129 MB) when it ended, so writes, and "
+                                         "the total, are a lower bound",
                          "algorithmic_bytes_per_launch": int(alg_bytes),
                          "bytes_rule": "per sample 1 read + 1 write (%d B each) + 1/8 mask; per window 4 count + 8 M/D"
                                        % esz,
@@ -537,6 +661,9 @@ def run_ours(args):
                          "timed_unit": "one plan call: the excision kernel, and for the noise plans also the "
                                        "noise_fill kernel that follows it"},
             "cpu_baseline": cpu,
+            "uneven60": subs.get("uneven60"),
+            "twelve60": subs.get("twelve60"),
+            "serve60": subs.get("serve60"),
             "mom": mom,
             "digital_copy": copies,
             "fused_format": fused,
@@ -557,9 +684,10 @@ def serve_desc(nstreams, seconds, feed):
             % (nstreams, seconds, feed))
 
 
-def run_serve(args):
+def run_serve(args, seconds=None, group=None, emit=True):
     """The serving workload: real-time streams paced at 800 Msps plus backfill requests through
-    rfi_server_*; reports chunk latency (scheduled arrival to done), RTF and throughput."""
+    rfi_server_*; reports chunk latency (scheduled arrival to done), RTF and throughput. With
+    emit False the line is returned instead of printed (and a given process group is kept)."""
     import heapq
 
     import numpy as np
@@ -574,7 +702,9 @@ def run_serve(args):
     rank, local, world = rdist.env_rank()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    group = rdist.Group("nccl" if world > 1 else None, device=dev)
+    own_group = group is None
+    if own_group:
+        group = rdist.Group("nccl" if world > 1 else None, device=dev)
     W, RATE = 16384, 800e6
     w = workloads.serve60(window=W, nstreams=args.streams)
     v = w.variants[0]
@@ -608,7 +738,7 @@ def run_serve(args):
         warm.close()
     srv = rfi.Server(8, [W] * S, 1 << 26, v.k, v.mode, v.const, v.seed, 40 * 10 ** 9, nslots, 1024,
                      stream_id=sids)
-    T = args.serve_seconds
+    T = args.serve_seconds if seconds is None else seconds
     # arrivals: per stream, chunk sizes log-uniform; a chunk arrives when its last sample does
     heap = []
     produced = [0] * S
@@ -731,8 +861,11 @@ def run_serve(args):
             "gpu_launches": int(st.passes) * 2,
             "clocks": clk,
         }
+        if not emit:
+            return line
         print(json.dumps(line), flush=True)
-    group.close()
+    if own_group:
+        group.close()
     return 0
 
 
@@ -752,6 +885,10 @@ def make_parser():
     ap.add_argument("--no-mom", action="store_true")
     ap.add_argument("--no-copies", action="store_true")
     ap.add_argument("--no-fused", action="store_true")
+    ap.add_argument("--no-subs", action="store_true",
+                    help="leave out the uneven60, twelve60 and serve60 sub-objects of the gwb60 line")
+    ap.add_argument("--sub-steps", type=int, default=10)
+    ap.add_argument("--sub-serve-seconds", type=float, default=2.0)
     ap.add_argument("--workload", choices=["gwb60", "twelve60", "uneven60", "serve60"], default="gwb60")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--feed", choices=["device", "host"], default="device")

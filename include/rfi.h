@@ -265,9 +265,11 @@ RFI_API rfi_status rfi_plan_destroy(rfi_plan_t plan);
  * Same computation and layouts as rfi_plan_create + rfi_excise + rfi_stats with the batched
  * form, but with no plan: desc describes the call (flags 0 or RFI_PLAN_BATCHED; desc->shape is
  * ignored, a fixed launch shape is used), and the persistent kernel's work list, segment table
- * and counters live in one fixed device array inside the library (about 1.1 MiB, reserved on
- * every GPU that loads the library until the process exits). Nothing is allocated, on the
- * device or the host. median/mad (nullable) receive the per-window M and D directly.
+ * and counters live in one fixed device array inside the library of RFI_NOALLOC_SCRATCH_BYTES
+ * (1,054,976 bytes: 256 of counters, a 96-byte record per stream and a 16-byte entry per tile,
+ * at the limits below), reserved on every GPU that loads the library until the process exits.
+ * Nothing is allocated, on the device or the host. median/mad (nullable) receive the
+ * per-window M and D directly.
  *
  * Limits: at most RFI_NOALLOC_MAX_STREAMS streams and RFI_NOALLOC_MAX_TILES work-list entries
  * (a tile holds as many whole windows as fit in a stage of up to 227 KiB); beyond them the call
@@ -278,9 +280,16 @@ RFI_API rfi_status rfi_plan_destroy(rfi_plan_t plan);
  * it keeps the last call's contents (the counters are cleared at the start of each call), so
  * calls that overlap on the GPU race: serialise them. Asynchronous on `stream` unless totals is
  * non-NULL, in which case the call synchronises `stream`, fills *totals and returns the device
- * status (RFI_OK, RFI_ERR_SAMPLE_RANGE, RFI_ERR_TIMEOUT). */
+ * status (RFI_OK, RFI_ERR_SAMPLE_RANGE, RFI_ERR_TIMEOUT). Device-detected errors (a 12-bit
+ * sample out of range, a bounded wait that timed out) are reported ONLY that way: with totals
+ * NULL nothing reads the status word, and the next call clears it.
+ *
+ * A CUDA error that an earlier call of the caller's left pending (cudaPeekAtLastError) makes
+ * the call return RFI_ERR_CUDA before it enqueues anything; the error is left in place for the
+ * caller to read. */
 #define RFI_NOALLOC_MAX_STREAMS 64
 #define RFI_NOALLOC_MAX_TILES 65536
+#define RFI_NOALLOC_SCRATCH_BYTES (256 + 96 * RFI_NOALLOC_MAX_STREAMS + 16 * RFI_NOALLOC_MAX_TILES)
 RFI_API rfi_status rfi_excise_noalloc(const rfi_plan_desc *desc, const void *const *in, void *const *out,
                                       uint32_t *const *mask, uint32_t *const *counts,
                                       int32_t *const *median, int32_t *const *mad, rfi_totals *totals,

@@ -34,6 +34,9 @@ RFI_PLAN_NOISE_PASS = 0x40
 RFI_OUT_SAME, RFI_OUT_F16, RFI_OUT_BF16 = 0, 1, 2
 RFI_MAX_COPIES = 8
 RFI_PLAN_INJECT_TIMEOUT = 0x100
+RFI_NOALLOC_MAX_STREAMS = 64
+RFI_NOALLOC_MAX_TILES = 65536
+RFI_NOALLOC_SCRATCH_BYTES = 256 + 96 * RFI_NOALLOC_MAX_STREAMS + 16 * RFI_NOALLOC_MAX_TILES
 
 
 class RfiLaunchShape(ctypes.Structure):

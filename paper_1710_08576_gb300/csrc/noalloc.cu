@@ -14,7 +14,10 @@
 //     are cleared at the start of each call. Calls whose work overlaps on the GPU (two streams,
 //     two threads) race on the array and must be serialised by the caller;
 //   - at most kMaxStreams streams and kMaxTiles work-list entries per call; larger requests are
-//     rejected with RFI_ERR_UNSUPPORTED before anything is enqueued.
+//     rejected with RFI_ERR_UNSUPPORTED before anything is enqueued;
+//   - device-detected errors are returned only when the caller asks for the totals (which
+//     synchronises the stream); a CUDA error already pending on entry is left in place and the
+//     call returns RFI_ERR_CUDA without enqueueing anything.
 
 #include <algorithm>
 #include <cmath>
@@ -43,6 +46,7 @@ constexpr size_t kCtrBytes = 256;
 constexpr size_t kSegBytes = sizeof(Seg) * kMaxStreams;
 constexpr size_t kTileBytes = sizeof(Tile) * kMaxTiles;
 constexpr size_t kScratchBytes = kCtrBytes + kSegBytes + kTileBytes;
+static_assert(kScratchBytes == RFI_NOALLOC_SCRATCH_BYTES, "the header states the array's size");
 
 static __device__ __align__(256) uint8_t g_scratch[kScratchBytes];
 
@@ -133,6 +137,10 @@ extern "C" rfi_status rfi_excise_noalloc(const rfi_plan_desc *d, const void *con
         if (mad && mad[i] && (reinterpret_cast<uintptr_t>(mad[i]) & 3)) return RFI_ERR_ALIGNMENT;
         maxwb = std::max<int64_t>(maxwb, std::min<int64_t>(d->window_len[i], d->stream_len[i]) * bps);
     }
+
+    // ---- an error pending from the caller's earlier CUDA work is left for the caller: refuse
+    // before enqueueing anything, so that the launch checks below see only this call's launches
+    if (cudaPeekAtLastError() != cudaSuccess) return RFI_ERR_CUDA;
 
     // ---- launch shape (fixed; no tuning runs, which would need scratch buffers)
     Shape sh{};

@@ -71,9 +71,9 @@ int main(void) {
 def test_constants_match_header(tmp_path):
     """Every RFI_* enum value and flag of the header equals the binding's constant of that name."""
     text = open(HEADER).read()
-    names = sorted(set(re.findall(r"#define\s+(RFI_(?:PLAN|MAX)_\w+)\s", text)) |
+    names = sorted(set(re.findall(r"#define\s+(RFI_(?:PLAN|MAX|NOALLOC)_\w+)\s", text)) |
                    set(re.findall(r"\b(RFI_(?:OK|ERR_\w+|REPLACE_\w+|OUT_\w+))\s*=", text)))
-    assert "RFI_PLAN_NOISE_PASS" in names and "RFI_ERR_BUSY" in names and "RFI_OUT_BF16" in names
+    assert "RFI_PLAN_NOISE_PASS" in names and "RFI_NOALLOC_SCRATCH_BYTES" in names and "RFI_ERR_BUSY" in names and "RFI_OUT_BF16" in names
     src = tmp_path / "consts.c"
     src.write_text("#include <stdio.h>\n#include \"rfi.h\"\nint main(void) {\n" +
                    "".join('  printf("%%s %%lld\\n", "%s", (long long)(%s));\n' % (n, n) for n in names) +

@@ -5,6 +5,9 @@ D of every window), the sliding lower median of the last k_mom MADs of each stre
 persistent kernel in its apply mode (Eq. 1 and Eq. 2 around each window's M with its MoM). Every
 output is compared with oracle.excise_mom: samples, mask, counts, M, D and the MoM itself.
 """
+import os
+import time
+
 import numpy as np
 import pytest
 
@@ -217,3 +220,16 @@ def test_mom_full_size_paper_configuration(cuda, rfi):
         flagged = np.unpackbits(g["mask"].view(np.uint8), bitorder="little").astype(bool)
         assert not np.any(changed & ~flagged)  # only flagged samples change
     assert totals.flagged == total
+    # whole streams against the oracle, every window, in both digital-noise forms (the benchmark
+    # runs the MoM plan with RFI_PLAN_NOISE_PASS)
+    st2, totals2, got2 = _gpu(rfi, xs, [W] * S, 8, 3.0, 3, K, seed=7,
+                              flags=rfi.RFI_PLAN_GRAPH | rfi.RFI_PLAN_NOISE_PASS)
+    assert st2 == rfi.RFI_OK and totals2.flagged == totals.flagged
+    threads = os.cpu_count() or 1
+    t0 = time.time()
+    for s in (0, 13, 37, 59):
+        ref = oracle.excise_mom(xs[s], W, 3.0, 3, K, seed=7, stream_id=s, threads=threads)
+        assert ref["status"] == 0
+        _check(got[s], ref, "stream %d one-pass" % s)
+        _check(got2[s], ref, "stream %d noise pass" % s)
+    print("\nMoM whole-stream comparison: 4 streams in %.1f s on %d threads" % (time.time() - t0, threads))

@@ -7,9 +7,12 @@ library. This file is collected last so that a failure here does not hide the ot
 Both calls below must match the plan path (rfi_plan_create / rfi_excise / rfi_stats) bit for
 bit, the second one after the first has left its contents in the shared array.
 """
+import os
+
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from synth import workloads
 
@@ -80,3 +83,68 @@ def test_noalloc_rejects_requests_beyond_its_limits(rfi):
     d = rfi.make_desc(8, [1024], [0], 3.0, 0)
     st, _ = rfi.rfi_excise_noalloc(d, [1], [1])
     assert st == rfi.RFI_ERR_INVALID_ARG
+
+
+def _noalloc_vs_oracle(rfi, bits, xs, wins, k, mode, seed, sids=None):
+    """rfi_excise_noalloc on device copies of xs, every output compared with the oracle run on
+    each whole stream (windows from absolute sample 0, as the call takes them)."""
+    import torch
+    sids = list(range(len(xs))) if sids is None else sids
+    dev_in = [torch.from_numpy(x).cuda() for x in xs]
+    out = [torch.full_like(t, 77) for t in dev_in]
+    nwin = [-(-x.size // W) for x, W in zip(xs, wins)]
+    masks = [torch.full((n * ((W + 31) // 32),), -1, dtype=torch.int32, device="cuda") for n, W in zip(nwin, wins)]
+    counts = [torch.full((n,), -1, dtype=torch.int32, device="cuda") for n in nwin]
+    meds = [torch.full((n,), -99, dtype=torch.int32, device="cuda") for n in nwin]
+    mads = [torch.full((n,), -99, dtype=torch.int32, device="cuda") for n in nwin]
+    d = rfi.make_desc(bits, [x.size for x in xs], wins, k, mode, 0, seed, stream_id=sids)
+    st, totals = rfi.rfi_excise_noalloc(d, dev_in, out, masks, counts, meds, mads)
+    torch.cuda.synchronize()
+    assert st == 0, rfi.rfi_status_string(st)
+    assert totals.windows == sum(nwin)
+    flagged = 0
+    for i, x in enumerate(xs):
+        r = oracle.excise(x, wins[i], k, mode, seed=seed, stream_id=sids[i], bits=bits,
+                          threads=os.cpu_count() or 1)
+        assert r["status"] == 0
+        got = dict(z=out[i].cpu().numpy(), mask=masks[i].cpu().numpy().view(np.uint32),
+                   counts=counts[i].cpu().numpy().view(np.uint32), median=meds[i].cpu().numpy(),
+                   mad=mads[i].cpu().numpy())
+        for key in got:
+            if not np.array_equal(got[key], r[key]):
+                bad = np.flatnonzero(got[key] != r[key])
+                raise AssertionError("stream %d (W %d) %s differs at %d positions, first %s"
+                                     % (i, wins[i], key, bad.size, bad[:8]))
+        flagged += int(r["counts"].sum())
+    assert totals.flagged == flagged
+
+
+def test_noalloc_against_oracle_unaligned_mixed_and_largest_windows(cuda, rfi):
+    """Windows that are not a multiple of 16 bytes (one window per tile, loaded by lanes), 12-bit
+    windows of 1000 samples (8 per tile), a different window per stream, and the largest window
+    (65536 samples, one per 64 KiB stage), against the oracle directly."""
+    xs = _streams(8, [40 * 1000 + 999, 30 * 4096 + 5, 3 * 65536 + 4097, 200 * 512, 65536], 21)
+    _noalloc_vs_oracle(rfi, 8, xs, [1000, 4096, 65536, 512, 65536], 3.0, 3, 7)
+    xs = _streams(12, [50 * 1000 + 17, 40 * 1001 + 3], 22)
+    _noalloc_vs_oracle(rfi, 12, xs, [1000, 1001], 3.5, 3, 9, sids=[5, 6])
+
+
+def test_noalloc_doubles_the_stage_when_the_work_list_is_full(cuda, rfi):
+    """16 streams of 2^26 + 4096 int8 samples in 4096-sample windows: at the first stage size
+    (16 KiB, 4 windows per tile) the work list would need 16 * 4097 = 65552 entries, more than
+    the fixed array holds, so the call doubles the stage (8 windows per tile, 32784 entries).
+    Every output against the oracle."""
+    W, n = 4096, (1 << 26) + 4096
+    per = 16384 // W
+    assert 16 * -(-(n // W) // per) > rfi.RFI_NOALLOC_MAX_TILES >= 16 * -(-(n // W) // (2 * per))
+    xs = _streams(8, [n] * 16, 23)
+    _noalloc_vs_oracle(rfi, 8, xs, [W] * 16, 3.0, 3, 7)
+
+
+def test_noalloc_rejects_a_work_list_beyond_its_array(rfi):
+    """70 000 windows of 1000 int8 samples need one work-list entry each (a window that is not a
+    multiple of 16 bytes is a tile of its own) at every stage size: more than the fixed array
+    holds, so the call returns RFI_ERR_UNSUPPORTED before it touches the (dummy) buffers."""
+    d = rfi.make_desc(8, [70000 * 1000], [1000], 3.0, 0)
+    st, _ = rfi.rfi_excise_noalloc(d, [16], [16])
+    assert st == rfi.RFI_ERR_UNSUPPORTED
