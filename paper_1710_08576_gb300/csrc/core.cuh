@@ -251,6 +251,16 @@ struct ApplyTile {
     uint32_t count[kApplyTileWindows];
 };
 
+// Multi-window tiles (8-bit, one consumer group): up to kMultiWindows small windows are
+// histogrammed at once, window slot g in lanes 8g..8g+7 of the lane-striped table, so that one
+// reduce, one set of barriers and parallel searches serve them all. Their cumulative counts are
+// slot g's kCumWords words at cum + g * kCumWords.
+constexpr int kMultiWindows = 4;
+struct MultiTile {
+    RepShared rep[kMultiWindows];
+    uint32_t count[kMultiWindows];
+};
+
 struct Ctl {
     uint32_t warp_tot[32];
     RepShared rep;       // threshold and replacement values of the current window
@@ -283,6 +293,7 @@ struct Shm {
     uint16_t *nlist;     // digital noise work area (or null): int8, the window's chunk flag masks;
                          // 12-bit, the positions of its flagged samples
     ApplyTile *at;       // apply passes: the current tile's thresholds and counts (or null)
+    struct MultiTile *mt;  // 8-bit, one group: state of a multi-window tile (or null)
 };
 
 // Capacity of the digital-noise work area (16-bit entries: int8 chunk masks of windows up to
@@ -1252,37 +1263,25 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
     return true;
 }
 
-// ------------------------------------------------------------------ apply pass over a tile
-// The apply pass (Eq. 1 and Eq. 2 around each window's given M with its given dispersion, as
-// for the median of MADs of Eq. 3) over a whole tile of nw full int8 windows of one segment,
-// W = 2^lw >= 512 samples each, 16-byte aligned. One barrier for the tile's thresholds (thread
-// k builds window k's), then the replace pass over all of the tile's chunks: a warp's round of
-// 32 chunks lies in one window, whose flag count takes one shared atomic. Digital noise is the
-// deferred scheme of noise_deferred8 over the tile, each sample taking its window's M and
-// spread. The last warp writes the tile's counts and releases the stage. Against one window
-// at a time this saves three barriers per window and keeps every thread busy on windows of
-// 4096 samples, which give 256 threads one chunk each.
-template <int MODE, int T>
-__device__ bool process_tile_apply8(const Shm &sm, const uint8_t *stage, const Tile &tl, const Seg &sg,
-                                    const int2 *amd, const Params &p, int tid, int par, int lw,
-                                    uint32_t release_bar, bool stage_ok) {
+// ------------------------------------------------------------------ replace pass over a tile
+// Eq. 1 and Eq. 2 over a whole tile of nw full int8 windows of one segment, W = 2^lw samples
+// each, 16-byte aligned, window k (of the tile) with the thresholds reps[k] already in shared
+// memory: the replace pass over all of the tile's chunks (a warp's round of 32 chunks lies in
+// one window, whose flag count takes one shared atomic), then the digital noise numbered over
+// the tile as in noise_deferred8, each sample taking its window's M and spread. The last warp
+// writes the windows' counts from cnt (and zeroes them) and, when release_bar != 0, releases
+// the stage. Windows start at window w0 of the segment.
+template <int RMODE, int T>
+__device__ void replace_tile8(const Shm &sm, const uint8_t *stage, const Seg &sg, uint32_t w0, int nw, int lw,
+                              const RepShared *reps, uint32_t *cnt, const Params &p, int tid, int par,
+                              uint32_t release_bar) {
     constexpr int NW = T / 32;
-    constexpr int RMODE = MODE & 3;
     const int lane = tid & 31, warp = tid >> 5;
-    const int nw = static_cast<int>(tl.nw);
-    // every thread has finished the previous tile or window (its thresholds, counts, noise
-    // work area) before this barrier
-    if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
-    RepShared *reps = sm.at->rep;
-    uint32_t *cnt = sm.at->count;
-    if (tid < nw) reps[tid] = make_rep<8>(amd[tid].x, amd[tid].y, p.kq, p.cval);
-    named_bar(sm.bar_id, T);
-
     const int lcw = lw - 4;  // log2 of the chunks per window
     const int nchunks = nw << lcw;
     const uint4 *d4 = reinterpret_cast<const uint4 *>(stage);
-    uint8_t *out = sg.out + (static_cast<int64_t>(tl.w0) << lw);
-    uint16_t *mk = sg.mask ? reinterpret_cast<uint16_t *>(sg.mask + static_cast<int64_t>(tl.w0) * sg.mask_words)
+    uint8_t *out = sg.out + (static_cast<int64_t>(w0) << lw);
+    uint16_t *mk = sg.mask ? reinterpret_cast<uint16_t *>(sg.mask + static_cast<int64_t>(w0) * sg.mask_words)
                            : nullptr;
     uint32_t own = 0;  // this thread's flagged samples (noise numbering)
     for (int c0 = warp * 32; c0 < nchunks; c0 += T) {
@@ -1329,7 +1328,7 @@ __device__ bool process_tile_apply8(const Shm &sm, const uint8_t *stage, const T
         firsts[tid] = static_cast<uint16_t>(first < 65535u ? first : 65535u);
         named_bar(sm.bar_id, T);
         const KeysPre key{p};
-        const int64_t abs0 = sg.abs0 + (static_cast<int64_t>(tl.w0) << lw);
+        const int64_t abs0 = sg.abs0 + (static_cast<int64_t>(w0) << lw);
         for (uint32_t q = static_cast<uint32_t>(tid); q < total; q += T) {
             int u = 0;
 #pragma unroll
@@ -1361,13 +1360,156 @@ __device__ bool process_tile_apply8(const Shm &sm, const uint8_t *stage, const T
             for (int k = 0; k < nw; ++k) {
                 const uint32_t ck = cnt[k];
                 cnt[k] = 0u;
-                if (sg.counts) sg.counts[tl.w0 + k] = ck;
+                if (sg.counts) sg.counts[w0 + k] = ck;
                 tot += ck;
             }
             sm.ctl->flagged += tot;
             if (release_bar) mbar_arrive(release_bar);
         }
     }
+}
+
+// ------------------------------------------------------------------ apply pass over a tile
+// The apply pass (Eq. 1 and Eq. 2 around each window's given M with its given dispersion, as
+// for the median of MADs of Eq. 3) over a whole tile of nw full int8 windows of one segment,
+// W = 2^lw >= 512 samples each, 16-byte aligned: one barrier for the tile's thresholds (thread
+// k builds window k's), then replace_tile8. Against one window at a time this saves three
+// barriers per window and keeps every thread busy on windows of 4096 samples, which give 256
+// threads one chunk each.
+template <int MODE, int T>
+__device__ bool process_tile_apply8(const Shm &sm, const uint8_t *stage, const Tile &tl, const Seg &sg,
+                                    const int2 *amd, const Params &p, int tid, int par, int lw,
+                                    uint32_t release_bar, bool stage_ok) {
+    const int nw = static_cast<int>(tl.nw);
+    // every thread has finished the previous tile or window (its thresholds, counts, noise
+    // work area) before this barrier
+    if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
+    RepShared *reps = sm.at->rep;
+    if (tid < nw) reps[tid] = make_rep<8>(amd[tid].x, amd[tid].y, p.kq, p.cval);
+    named_bar(sm.bar_id, T);
+    replace_tile8<MODE & 3, T>(sm, stage, sg, tl.w0, nw, lw, reps, sm.at->count, p, tid, par, release_bar);
+    return true;
+}
+
+// ------------------------------------------------------------------ multi-window tiles
+// Histogram of up to kMultiWindows windows of 2^lw samples at once: window slot g (< nw) is
+// counted by lanes 8g..8g+7 of every warp into their own columns of the lane-striped table, so
+// the atomics stay conflict-free and the slots never mix.
+template <int T>
+__device__ __forceinline__ void hist8_multi(const Shm &sm, const uint8_t *stage, int lw, int nw, int tid) {
+    constexpr int TS = T / kMultiWindows;  // threads per slot
+    const int lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 3;
+    if (g >= nw) return;
+    const int i = warp * 8 + (lane & 7);
+    const uint32_t lb = sm.hist_s + 4u * lane;
+    const uint4 *d4 = reinterpret_cast<const uint4 *>(stage + (g << lw));
+    const int nch = 1 << (lw - 4);
+    int c = i;
+    for (; c + TS < nch; c += 2 * TS) {
+        const uint4 a = d4[c], b = d4[c + TS];
+        hist8_word<128>(lb, a.x); hist8_word<128>(lb, a.y); hist8_word<128>(lb, a.z); hist8_word<128>(lb, a.w);
+        hist8_word<128>(lb, b.x); hist8_word<128>(lb, b.y); hist8_word<128>(lb, b.z); hist8_word<128>(lb, b.w);
+    }
+    if (c < nch) {
+        const uint4 a = d4[c];
+        hist8_word<128>(lb, a.x); hist8_word<128>(lb, a.y); hist8_word<128>(lb, a.z); hist8_word<128>(lb, a.w);
+    }
+}
+
+// Counts of every slot from the table, which is zeroed as it is read (the 128-byte row of raw
+// byte u holds lane l's count at word l; slot g's lanes are the row's 16-byte groups 2g, 2g+1).
+// The eight threads tid & ~7 .. tid | 7 read the eight 16-byte groups of the same row, so the
+// reads and clears are free of bank conflicts; thread pairs combine their groups by a shuffle.
+template <int T>
+__device__ __forceinline__ void reduce8_multi(const Shm &sm, int tid) {
+    constexpr int RPT = 256 / (T / 8);  // rows per thread
+    const int p = tid & 7;
+    const int r0 = (tid >> 3) * RPT;
+    uint4 *tab = reinterpret_cast<uint4 *>(sm.hist);
+    uint32_t *cumg = sm.cum + (p >> 1) * Geo<8>::kCumWords;
+#pragma unroll 4
+    for (int k = 0; k < RPT; ++k) {
+        const int row = r0 + k;
+        uint4 *a = tab + row * 8 + p;
+        const uint4 v = *a;
+        *a = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t sum = v.x + v.y + v.z + v.w;
+        sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 1);
+        if ((p & 1) == 0) cumg[pad32(row ^ 128)] = sum;
+    }
+}
+
+// One warp: the inclusive scan of a slot's 256 counts in place (8 consecutive bins per lane),
+// then its lower median bin and MAD (the searches of phase_scan8_warp and phase_search), and the
+// threshold and replacement values into *rep (lane 0). Returns nothing; M and D are in *rep.
+__device__ __forceinline__ void scan_search8(uint32_t *cum, int n, int lane, int64_t kq, int32_t cval,
+                                             RepShared *rep) {
+    uint32_t c[8];
+    uint32_t run = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        run += cum[pad32(lane * 8 + j)];
+        c[j] = run;
+    }
+    uint32_t inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t excl = inc - run;
+    const uint32_t half = static_cast<uint32_t>((n + 1) >> 1);
+    int found = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t v = c[j] + excl;
+        const uint32_t before = (j ? c[j - 1] : 0u) + excl;
+        cum[pad32(lane * 8 + j)] = v;
+        if (v >= half && before < half) found = lane * 8 + j + 1;
+    }
+    // the median bin is the one lane that found it; the others hold 0
+    const int mb = static_cast<int>(__reduce_max_sync(0xFFFFFFFFu, static_cast<uint32_t>(found))) - 1;
+    __syncwarp();
+    const int d = warp_search<256>(lane, [&](int dd) {
+        const int hi = mb + dd < 255 ? mb + dd : 255;
+        const int lo = mb - dd - 1;
+        const uint32_t f = cum[pad32(hi)] - (lo >= 0 ? cum[pad32(lo)] : 0u);
+        return f >= half;
+    });
+    if (lane == 0) *rep = make_rep<8>(mb - Geo<8>::kOffset, d, kq, cval);
+}
+
+// A tile of nw (2 <= nw <= kMultiWindows) full int8 windows of 2^lw samples, 16-byte aligned,
+// in shared memory at stage, for the plain excision modes (MODE 0..3) or the estimation pass of
+// the Median of MAD (kModeStats). The histogram table must be zero on entry and is zero again
+// after the reduce. Barriers: after the histogram (a bar.red.or that also agrees on a timeout),
+// after the reduce, and, for excision, after the searches; warp g searches window g. M and D go
+// straight to the segment's arrays. release_bar (nonzero for the tile's last windows) releases
+// the stage: after the histogram for kModeStats, else after the replace pass.
+template <int MODE, int T>
+__device__ bool process_tile_multi8(const Shm &sm, const uint8_t *stage, const Seg &sg, uint32_t w0, int nw, int lw,
+                                    const Params &p, int tid, int par, uint32_t release_bar, bool stage_ok) {
+    constexpr bool STATS = (MODE & kModeStats) != 0;
+    const int lane = tid & 31, warp = tid >> 5;
+    int32_t *const med = sg.med, *const mad = sg.mad;  // sg lives in the stage descriptor
+    if (stage_ok) hist8_multi<T>(sm, stage, lw, nw, tid);
+    if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
+    if (STATS && tid == 0 && release_bar) mbar_arrive(release_bar);
+    reduce8_multi<T>(sm, tid);
+    named_bar(sm.bar_id, T);
+    if (warp < nw) {
+        RepShared *rep = &sm.mt->rep[warp];
+        scan_search8(sm.cum + warp * Geo<8>::kCumWords, 1 << lw, lane, p.kq, p.cval, rep);
+        __syncwarp();
+        if (lane == 0) {
+            if (med) med[w0 + warp] = rep->M;
+            if (mad) mad[w0 + warp] = rep->D;
+        }
+    }
+    if (STATS) return true;
+    named_bar(sm.bar_id, T);
+    replace_tile8<MODE & 3, T>(sm, stage, sg, w0, nw, lw, sm.mt->rep, sm.mt->count, p, tid, par, release_bar);
     return true;
 }
 

@@ -30,6 +30,11 @@ constexpr int kModeCopies = 32;
 constexpr int kModeF16 = 64;
 constexpr int kModeBF16 = 128;
 constexpr int kMaxCopies = 8;
+// Flag bit of the multi-window form (8-bit, one consumer group; plain excision or the estimation
+// pass): tiles of several small windows of 2^l samples (512..8192) are histogrammed together and
+// share one reduce and one set of barriers. A separate instantiation, so that plans without such
+// windows keep the plain kernel's shared-memory layout and code.
+constexpr int kModeMulti = 256;
 
 // One variant of a digital-copy pass.
 struct Variant {

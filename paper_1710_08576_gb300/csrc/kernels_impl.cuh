@@ -36,6 +36,7 @@ struct Layout {
     int amd;                  // apply passes: per stage, {M, dispersion} of its windows (0: none)
     int atile;                // apply passes: thresholds and counts of the current tile (0: none)
     int cps;                  // digital copy: per-variant state inside a group block (0: none)
+    int mt;                   // 8-bit plain excision and estimation: multi-window tile state (0: none)
     int stage;      // first stage buffer; group g stage s at stage + (g * stages + s) * stage_bytes
     int total;
 };
@@ -44,8 +45,10 @@ template <int BITS>
 __host__ __device__ inline Layout layout(int ncopies, int stages, int stage_bytes, int cw, int groups, int mode) {
     Layout L;
     L.grp = (mode & kModeApply) ? 0 : align_up(Geo<BITS>::hist_bytes(ncopies, groups), 128);
+    // multi-window tiles: 8-bit, one group, plain excision or the estimation pass
+    const bool multi = BITS == 8 && groups == 1 && (mode & kModeMulti) != 0;
     L.cum = 0;
-    L.ctl = align_up(Geo<BITS>::kCumWords * 4, 128);
+    L.ctl = align_up(Geo<BITS>::kCumWords * 4 * (multi ? kMultiWindows : 1), 128);
     L.bar = align_up(L.ctl + static_cast<int>(sizeof(Ctl)), 128);
     L.meta = align_up(L.bar + (2 * kMaxStages + 1) * 8, 128);
     const int meta_end = align_up(L.meta + kMaxStages * static_cast<int>(sizeof(StageMeta)), 128);
@@ -61,7 +64,9 @@ __host__ __device__ inline Layout layout(int ncopies, int stages, int stage_byte
     const int amd_end = apply ? align_up(L.atile + static_cast<int>(sizeof(ApplyTile)), 128) : list_end;
     const bool copies = (mode & kModeCopies) != 0;
     L.cps = copies ? amd_end : 0;
-    L.grp_size = copies ? align_up(amd_end + static_cast<int>(sizeof(CopyShared)), 128) : amd_end;
+    const int cps_end = copies ? align_up(amd_end + static_cast<int>(sizeof(CopyShared)), 128) : amd_end;
+    L.mt = multi ? cps_end : 0;
+    L.grp_size = multi ? align_up(cps_end + static_cast<int>(sizeof(MultiTile)), 128) : cps_end;
     L.stage = L.grp + groups * L.grp_size;
     L.total = L.stage + groups * stages * stage_bytes;
     return L;
@@ -82,6 +87,7 @@ __device__ __forceinline__ Shm group_view(uint8_t *smem, const Layout &L, int g,
     sm.nlist = L.nlist ? reinterpret_cast<uint16_t *>(gb + L.nlist) : nullptr;
     sm.cp = L.cps ? reinterpret_cast<CopyShared *>(gb + L.cps) : nullptr;
     sm.at = L.atile ? reinterpret_cast<ApplyTile *>(gb + L.atile) : nullptr;
+    sm.mt = L.mt ? reinterpret_cast<MultiTile *>(gb + L.mt) : nullptr;
     return sm;
 }
 
@@ -274,6 +280,8 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
     int par = 0;  // window parity
     bool timed_out = false;
     RowSums rs = {{0u, 0u}};
+    // the table holds the per-window path's running sums (multi-window tiles need it zero)
+    bool dirty = false;
     for (int it = 0;; ++it) {
         const int s = it % stages;
         const int u = it / stages;
@@ -313,6 +321,34 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
                 }
                 continue;
             }
+        }
+        if constexpr (BITS == 8 && G == 1 && (MODE & kModeMulti) != 0) {
+            // several small full windows of 2^lw samples: kMultiWindows at a time share the
+            // histogram table, the reduce, the barriers and the searches
+            const uint32_t W = static_cast<uint32_t>(sg.W);
+            if (sg.vec && tl.nw >= 2u && W >= 512u && W <= 8192u && (W & (W - 1u)) == 0u && tl.bytes == tl.nw * W) {
+                if (dirty) {
+                    zero_shared(sm.hist, 32768, tid, T);
+                    named_bar(sm.bar_id, T);
+                    dirty = false;
+                }
+                const int lw = 31 - __clz(static_cast<int>(W));
+                for (uint32_t k0 = 0; k0 < tl.nw && alive; k0 += kMultiWindows) {
+                    const int nwk = static_cast<int>(tl.nw - k0 < static_cast<uint32_t>(kMultiWindows) ? tl.nw - k0
+                                                                                                     : kMultiWindows);
+                    alive = process_tile_multi8<MODE & ~kModeMulti, T>(sm, stage + (k0 << lw), sg, tl.w0 + k0, nwk, lw, p,
+                                                                       tid, par,
+                                                         k0 + kMultiWindows >= tl.nw ? empty_bar(s) : 0u, true);
+                    par ^= 1;
+                }
+                rs = {{0u, 0u}};  // the reduce left the table zero
+                if (!alive) {
+                    timed_out = true;
+                    break;
+                }
+                continue;
+            }
+            dirty = true;
         }
         for (uint32_t k = 0; k < tl.nw && alive; ++k) {
             const int64_t widx = static_cast<int64_t>(tl.w0) + k;

@@ -68,7 +68,7 @@ rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req) {
     s.dynamic_tiles = (req && req->dynamic_tiles) ? req->dynamic_tiles : (uniform ? 2 : 1);
     const int want_ctas = (req && req->ctas_per_sm) ? req->ctas_per_sm : 4;  // as many as fit, up to 4
     // the shape is sized for the kernel with the histogram (the MoM stats pass)
-    const int kmode = P->kmom >= 2 ? kModeStats : plan_kernel_mode(P);
+    const int kmode = P->kmom >= 2 ? plan_stats_mode(P) : plan_kernel_mode(P);
     if (persistent_smem_bytes(P->bits, kmode, s) > 227u * 1024u) {
         if (req && req->stages) return RFI_ERR_UNSUPPORTED;
         while (s.stages > 1 && persistent_smem_bytes(P->bits, kmode, s) > 227u * 1024u) --s.stages;
@@ -224,7 +224,7 @@ rfi_status plan_enqueue_batched(rfi_plan_s *P, cudaStream_t st) {
     // Median of MAD (Eq. 3): M and D of every window, the sliding median of the MADs, then Eq. 1
     // and Eq. 2 with each window's M and its MoM (segment entries S..2S-1)
     const Params p = plan_params(P);
-    RFI_CUDA(launch_persistent(P->bits, kModeStats, P->shape, P->grid, P->d_segs, P->d_tiles, P->ntiles, p,
+    RFI_CUDA(launch_persistent(P->bits, plan_stats_mode(P), P->shape, P->grid, P->d_segs, P->d_tiles, P->ntiles, p,
                                &P->d_ctr->tile_counter, inject, st));
     RFI_CUDA(launch_mom(P->bits, P->d_mchunks, static_cast<int>(P->mchunks.size()), P->d_mad, P->d_mom, P->kmom,
                         st));
@@ -428,6 +428,15 @@ static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_va
     for (int i = 0; i < P->S; ++i) short_segs = short_segs && P->len[i] < (int64_t{1} << 31);
     P->fill = (P->flags & RFI_PLAN_NOISE_PASS) && P->mode == RFI_REPLACE_NOISE && !(P->flags & RFI_PLAN_PER_STREAM) &&
               !P->power && P->ncopy == 0 && P->out_format == RFI_OUT_SAME && short_segs;
+    // small windows of 2^l samples: the multi-window form of the 8-bit kernel (several windows
+    // per histogram, reduce and set of barriers)
+    if (P->bits == 8 && P->ncopy == 0 && !P->power && P->out_format == RFI_OUT_SAME &&
+        !(P->flags & RFI_PLAN_PER_STREAM)) {
+        for (int i = 0; i < P->S && !P->multi; ++i) {
+            const int32_t W = P->W[i];
+            P->multi = W >= 512 && W <= 8192 && (W & (W - 1)) == 0 && P->len[i] >= 2 * static_cast<int64_t>(W);
+        }
+    }
 
     rfi_status rs = RFI_OK;
     if (cudaGetDevice(&P->device) != cudaSuccess ||

@@ -55,6 +55,8 @@ struct rfi_plan_s {
     int32_t *d_mom = nullptr;
     // RFI_PLAN_POWER: {sum x^2, sum z^2} per window
     bool power = false;
+    // some stream has windows of 2^l samples, 512 <= 2^l <= 8192: the multi-window form
+    bool multi = false;
     uint64_t *d_pow = nullptr;
     int out_format = RFI_OUT_SAME;  // fused output format
     // digital noise as a second pass (noise_fill): the excision pass replaces with 0, then the
@@ -113,7 +115,11 @@ std::vector<T> part_args(const rfi_plan_s *P, size_t k, T const *all) {
 // Kernel mode of a per-window MAD plan (the power-metered form when RFI_PLAN_POWER is set).
 inline int plan_kernel_mode(const rfi_plan_s *P) {
     const int fmt = P->out_format == RFI_OUT_F16 ? kModeF16 : (P->out_format == RFI_OUT_BF16 ? kModeBF16 : 0);
-    return P->ncopy > 0 ? kModeCopies : ((P->fill && P->kmom < 2 ? 0 : P->mode) | (P->power ? kModePower : 0) | fmt);
+    if (P->ncopy > 0) return kModeCopies;
+    const int m = (P->fill && P->kmom < 2 ? 0 : P->mode) | (P->power ? kModePower : 0) | fmt;
+    return m | (P->multi && m < 4 ? kModeMulti : 0);
 }
+// Kernel mode of the estimation pass of a Median-of-MAD plan.
+inline int plan_stats_mode(const rfi_plan_s *P) { return kModeStats | (P->multi ? kModeMulti : 0); }
 
 }  // namespace rfi
