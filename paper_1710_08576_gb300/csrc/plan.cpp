@@ -479,6 +479,16 @@ static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_va
                 P->parts.push_back(child);
                 P->part_streams.push_back(c);
             }
+            P->part_st.assign(P->parts.size(), nullptr);
+            P->part_ev.assign(P->parts.size(), nullptr);
+            for (size_t k = 0; k < P->parts.size(); ++k) {
+                if ((k > 0 && cudaStreamCreateWithFlags(&P->part_st[k], cudaStreamNonBlocking) != cudaSuccess) ||
+                    cudaEventCreateWithFlags(&P->part_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+                    cudaGetLastError();
+                    rfi_plan_destroy(P);
+                    return RFI_ERR_CUDA;
+                }
+            }
             *out_plan = P;
             return RFI_OK;
         }
@@ -503,13 +513,22 @@ rfi_status rfi_excise(rfi_plan_t P, const void *const *in, void *const *out, uin
     if (!P) return RFI_ERR_INVALID_ARG;
     if (!P->parts.empty()) {
         if (!in || !out) return RFI_ERR_INVALID_ARG;
+        // part 0 on the caller's stream, the others on their own streams after a fork event;
+        // the caller's stream then waits for every part
+        cudaStream_t st0 = static_cast<cudaStream_t>(stream);
+        if (cudaEventRecord(P->part_ev[0], st0) != cudaSuccess) return RFI_ERR_CUDA;
         for (size_t k = 0; k < P->parts.size(); ++k) {
             const auto a = part_args<const void *>(P, k, in);
             const auto b = part_args<void *>(P, k, out);
             const auto m = part_args<uint32_t *>(P, k, mask);
             const auto c = part_args<uint32_t *>(P, k, counts);
+            cudaStream_t sk = k == 0 ? st0 : P->part_st[k];
+            if (k > 0 && cudaStreamWaitEvent(sk, P->part_ev[0], 0) != cudaSuccess) return RFI_ERR_CUDA;
             const rfi_status rs = rfi_excise(P->parts[k], a.data(), b.data(), mask ? m.data() : nullptr,
-                                             counts ? c.data() : nullptr, stream);
+                                             counts ? c.data() : nullptr, sk);
+            if (k > 0 && (cudaEventRecord(P->part_ev[k], sk) != cudaSuccess ||
+                          cudaStreamWaitEvent(st0, P->part_ev[k], 0) != cudaSuccess))
+                return RFI_ERR_CUDA;
             if (rs != RFI_OK) return rs;
         }
         P->last_windows = P->total_windows;
@@ -755,6 +774,10 @@ rfi_status rfi_plan_get_info(rfi_plan_t P, rfi_plan_info *info) {
 rfi_status rfi_plan_destroy(rfi_plan_t P) {
     if (!P) return RFI_OK;
     for (rfi_plan_s *c : P->parts) rfi_plan_destroy(c);
+    for (cudaStream_t s : P->part_st)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : P->part_ev)
+        if (e) cudaEventDestroy(e);
     plan_release_host_pipe(P);
     if (P->gexec) cudaGraphExecDestroy(P->gexec);
     if (P->graph) cudaGraphDestroy(P->graph);

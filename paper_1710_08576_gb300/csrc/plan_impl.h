@@ -82,6 +82,10 @@ struct rfi_plan_s {
     size_t host_pipe_bytes = 0;
     // a plan split by window-size class: one internal plan per class and its stream indices
     std::vector<rfi_plan_s *> parts;
+    // parts after the first run on their own streams, forked from and joined back into the
+    // caller's stream with events, so that one part's tail overlaps the next part's kernels
+    std::vector<cudaStream_t> part_st;
+    std::vector<cudaEvent_t> part_ev;  // [0]: the fork; [k]: part k's end
     std::vector<std::vector<int>> part_streams;
 };
 
