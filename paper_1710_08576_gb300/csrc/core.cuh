@@ -251,14 +251,15 @@ struct ApplyTile {
     uint32_t count[kApplyTileWindows];
 };
 
-// Multi-window tiles (8-bit, one consumer group): up to kMultiWindows small windows are
-// histogrammed at once, window slot g in lanes 8g..8g+7 of the lane-striped table, so that one
-// reduce, one set of barriers and parallel searches serve them all. Their cumulative counts are
-// slot g's kCumWords words at cum + g * kCumWords.
-constexpr int kMultiWindows = 4;
+// Multi-window tiles (8-bit, one consumer group): up to K (4 or 8) small windows are
+// histogrammed at once, window slot g in lanes (32/K)g .. (32/K)(g+1)-1 of the lane-striped
+// table, so that one reduce, one set of barriers and parallel searches serve them all. Their
+// cumulative counts (at most 8192, the largest window of this form) are 16-bit: slot g's
+// kCumWords entries at (uint16_t *)cum + g * kCumWords.
+constexpr int kMultiMax = 8;
 struct MultiTile {
-    RepShared rep[kMultiWindows];
-    uint32_t count[kMultiWindows];
+    RepShared rep[kMultiMax];
+    uint32_t count[kMultiMax];
 };
 
 struct Ctl {
@@ -1392,16 +1393,17 @@ __device__ bool process_tile_apply8(const Shm &sm, const uint8_t *stage, const T
 }
 
 // ------------------------------------------------------------------ multi-window tiles
-// Histogram of up to kMultiWindows windows of 2^lw samples at once: window slot g (< nw) is
-// counted by lanes 8g..8g+7 of every warp into their own columns of the lane-striped table, so
-// the atomics stay conflict-free and the slots never mix.
-template <int T>
+// Histogram of up to K windows of 2^lw samples at once: window slot g (< nw) is counted by the
+// 32/K lanes (32/K)g .. of every warp into their own columns of the lane-striped table, so the
+// atomics stay conflict-free and the slots never mix.
+template <int T, int K>
 __device__ __forceinline__ void hist8_multi(const Shm &sm, const uint8_t *stage, int lw, int nw, int tid) {
-    constexpr int TS = T / kMultiWindows;  // threads per slot
+    constexpr int LPS = 32 / K;  // lanes per slot
+    constexpr int TS = T / K;    // threads per slot
     const int lane = tid & 31, warp = tid >> 5;
-    const int g = lane >> 3;
+    const int g = lane / LPS;
     if (g >= nw) return;
-    const int i = warp * 8 + (lane & 7);
+    const int i = warp * LPS + (lane % LPS);
     const uint32_t lb = sm.hist_s + 4u * lane;
     const uint4 *d4 = reinterpret_cast<const uint4 *>(stage + (g << lw));
     const int nch = 1 << (lw - 4);
@@ -1418,16 +1420,19 @@ __device__ __forceinline__ void hist8_multi(const Shm &sm, const uint8_t *stage,
 }
 
 // Counts of every slot from the table, which is zeroed as it is read (the 128-byte row of raw
-// byte u holds lane l's count at word l; slot g's lanes are the row's 16-byte groups 2g, 2g+1).
-// The eight threads tid & ~7 .. tid | 7 read the eight 16-byte groups of the same row, so the
-// reads and clears are free of bank conflicts; thread pairs combine their groups by a shuffle.
-template <int T>
+// byte u holds lane l's count at word l; a slot's lanes are 8/K of the row's eight 16-byte
+// groups). The eight threads tid & ~7 .. tid | 7 read the eight groups of the same row, so the
+// reads and clears are free of bank conflicts; with four slots, thread pairs combine their
+// groups by a shuffle. Counts go to 16-bit arrays, 264 entries per slot (slot g's array starts
+// on bank 4g, so the stores of one row's slots do not collide either).
+template <int T, int K>
 __device__ __forceinline__ void reduce8_multi(const Shm &sm, int tid) {
+    static_assert(K == 4 || K == 8, "four or eight window slots");
     constexpr int RPT = 256 / (T / 8);  // rows per thread
     const int p = tid & 7;
     const int r0 = (tid >> 3) * RPT;
     uint4 *tab = reinterpret_cast<uint4 *>(sm.hist);
-    uint32_t *cumg = sm.cum + (p >> 1) * Geo<8>::kCumWords;
+    uint16_t *cumg = reinterpret_cast<uint16_t *>(sm.cum) + (K == 8 ? p : (p >> 1)) * Geo<8>::kCumWords;
 #pragma unroll 4
     for (int k = 0; k < RPT; ++k) {
         const int row = r0 + k;
@@ -1435,15 +1440,16 @@ __device__ __forceinline__ void reduce8_multi(const Shm &sm, int tid) {
         const uint4 v = *a;
         *a = make_uint4(0u, 0u, 0u, 0u);
         uint32_t sum = v.x + v.y + v.z + v.w;
-        sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 1);
-        if ((p & 1) == 0) cumg[pad32(row ^ 128)] = sum;
+        if (K == 4) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, 1);
+        if (K == 8 || (p & 1) == 0) cumg[pad32(row ^ 128)] = static_cast<uint16_t>(sum);
     }
 }
 
 // One warp: the inclusive scan of a slot's 256 counts in place (8 consecutive bins per lane),
 // then its lower median bin and MAD (the searches of phase_scan8_warp and phase_search), and the
-// threshold and replacement values into *rep (lane 0). Returns nothing; M and D are in *rep.
-__device__ __forceinline__ void scan_search8(uint32_t *cum, int n, int lane, int64_t kq, int32_t cval,
+// threshold and replacement values into *rep (lane 0). The counts and cumulative counts are
+// 16-bit (a window of this form has at most 8192 samples).
+__device__ __forceinline__ void scan_search8(uint16_t *cum, int n, int lane, int64_t kq, int32_t cval,
                                              RepShared *rep) {
     uint32_t c[8];
     uint32_t run = 0;
@@ -1465,7 +1471,7 @@ __device__ __forceinline__ void scan_search8(uint32_t *cum, int n, int lane, int
     for (int j = 0; j < 8; ++j) {
         const uint32_t v = c[j] + excl;
         const uint32_t before = (j ? c[j - 1] : 0u) + excl;
-        cum[pad32(lane * 8 + j)] = v;
+        cum[pad32(lane * 8 + j)] = static_cast<uint16_t>(v);
         if (v >= half && before < half) found = lane * 8 + j + 1;
     }
     // the median bin is the one lane that found it; the others hold 0
@@ -1474,37 +1480,38 @@ __device__ __forceinline__ void scan_search8(uint32_t *cum, int n, int lane, int
     const int d = warp_search<256>(lane, [&](int dd) {
         const int hi = mb + dd < 255 ? mb + dd : 255;
         const int lo = mb - dd - 1;
-        const uint32_t f = cum[pad32(hi)] - (lo >= 0 ? cum[pad32(lo)] : 0u);
+        const uint32_t f = static_cast<uint32_t>(cum[pad32(hi)]) - (lo >= 0 ? static_cast<uint32_t>(cum[pad32(lo)]) : 0u);
         return f >= half;
     });
     if (lane == 0) *rep = make_rep<8>(mb - Geo<8>::kOffset, d, kq, cval);
 }
 
-// A tile of nw (2 <= nw <= kMultiWindows) full int8 windows of 2^lw samples, 16-byte aligned,
-// in shared memory at stage, for the plain excision modes (MODE 0..3) or the estimation pass of
-// the Median of MAD (kModeStats). The histogram table must be zero on entry and is zero again
+// A tile of nw (1 <= nw <= K) full int8 windows of 2^lw samples, 16-byte aligned, in shared
+// memory at stage, for the plain excision modes (MODE 0..3) or the estimation pass of the
+// Median of MAD (kModeStats). The histogram table must be zero on entry and is zero again
 // after the reduce. Barriers: after the histogram (a bar.red.or that also agrees on a timeout),
-// after the reduce, and, for excision, after the searches; warp g searches window g. M and D go
-// straight to the segment's arrays. release_bar (nonzero for the tile's last windows) releases
-// the stage: after the histogram for kModeStats, else after the replace pass.
-template <int MODE, int T>
+// after the reduce, and, for excision, after the searches; warp w searches windows w, w + NW,
+// ... M and D go straight to the segment's arrays. release_bar (nonzero for the tile's last
+// windows) releases the stage: after the histogram for kModeStats, else after the replace pass.
+template <int MODE, int T, int K>
 __device__ bool process_tile_multi8(const Shm &sm, const uint8_t *stage, const Seg &sg, uint32_t w0, int nw, int lw,
                                     const Params &p, int tid, int par, uint32_t release_bar, bool stage_ok) {
     constexpr bool STATS = (MODE & kModeStats) != 0;
+    constexpr int NW = T / 32;
     const int lane = tid & 31, warp = tid >> 5;
     int32_t *const med = sg.med, *const mad = sg.mad;  // sg lives in the stage descriptor
-    if (stage_ok) hist8_multi<T>(sm, stage, lw, nw, tid);
+    if (stage_ok) hist8_multi<T, K>(sm, stage, lw, nw, tid);
     if (named_bar_or(sm.bar_id, T, !stage_ok)) return false;
     if (STATS && tid == 0 && release_bar) mbar_arrive(release_bar);
-    reduce8_multi<T>(sm, tid);
+    reduce8_multi<T, K>(sm, tid);
     named_bar(sm.bar_id, T);
-    if (warp < nw) {
-        RepShared *rep = &sm.mt->rep[warp];
-        scan_search8(sm.cum + warp * Geo<8>::kCumWords, 1 << lw, lane, p.kq, p.cval, rep);
+    for (int g = warp; g < nw; g += NW) {
+        RepShared *rep = &sm.mt->rep[g];
+        scan_search8(reinterpret_cast<uint16_t *>(sm.cum) + g * Geo<8>::kCumWords, 1 << lw, lane, p.kq, p.cval, rep);
         __syncwarp();
         if (lane == 0) {
-            if (med) med[w0 + warp] = rep->M;
-            if (mad) mad[w0 + warp] = rep->D;
+            if (med) med[w0 + g] = rep->M;
+            if (mad) mad[w0 + g] = rep->D;
         }
     }
     if (STATS) return true;

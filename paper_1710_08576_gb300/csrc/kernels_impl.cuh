@@ -48,7 +48,8 @@ __host__ __device__ inline Layout layout(int ncopies, int stages, int stage_byte
     // multi-window tiles: 8-bit, one group, plain excision or the estimation pass
     const bool multi = BITS == 8 && groups == 1 && (mode & kModeMulti) != 0;
     L.cum = 0;
-    L.ctl = align_up(Geo<BITS>::kCumWords * 4 * (multi ? kMultiWindows : 1), 128);
+    // (multi-window tiles: up to kMultiMax slots of 16-bit counts)
+    L.ctl = align_up(multi ? Geo<BITS>::kCumWords * 2 * kMultiMax : Geo<BITS>::kCumWords * 4, 128);
     L.bar = align_up(L.ctl + static_cast<int>(sizeof(Ctl)), 128);
     L.meta = align_up(L.bar + (2 * kMaxStages + 1) * 8, 128);
     const int meta_end = align_up(L.meta + kMaxStages * static_cast<int>(sizeof(StageMeta)), 128);
@@ -323,8 +324,8 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
             }
         }
         if constexpr (BITS == 8 && G == 1 && (MODE & kModeMulti) != 0) {
-            // several small full windows of 2^lw samples: kMultiWindows at a time share the
-            // histogram table, the reduce, the barriers and the searches
+            // several small full windows of 2^lw samples: eight (W <= 2048) or four at a time share
+            // the histogram table, the reduce, the barriers and the searches
             const uint32_t W = static_cast<uint32_t>(sg.W);
             if (sg.vec && tl.nw >= 2u && W >= 512u && W <= 8192u && (W & (W - 1u)) == 0u && tl.bytes == tl.nw * W) {
                 if (dirty) {
@@ -333,12 +334,16 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
                     dirty = false;
                 }
                 const int lw = 31 - __clz(static_cast<int>(W));
-                for (uint32_t k0 = 0; k0 < tl.nw && alive; k0 += kMultiWindows) {
-                    const int nwk = static_cast<int>(tl.nw - k0 < static_cast<uint32_t>(kMultiWindows) ? tl.nw - k0
-                                                                                                     : kMultiWindows);
-                    alive = process_tile_multi8<MODE & ~kModeMulti, T>(sm, stage + (k0 << lw), sg, tl.w0 + k0, nwk, lw, p,
-                                                                       tid, par,
-                                                         k0 + kMultiWindows >= tl.nw ? empty_bar(s) : 0u, true);
+                const uint32_t K = W <= 2048u ? 8u : 4u;
+                for (uint32_t k0 = 0; k0 < tl.nw && alive; k0 += K) {
+                    const int nwk = static_cast<int>(tl.nw - k0 < K ? tl.nw - k0 : K);
+                    const uint32_t rel = k0 + K >= tl.nw ? empty_bar(s) : 0u;
+                    if (K == 8u)
+                        alive = process_tile_multi8<MODE & ~kModeMulti, T, 8>(sm, stage + (k0 << lw), sg, tl.w0 + k0,
+                                                                              nwk, lw, p, tid, par, rel, true);
+                    else
+                        alive = process_tile_multi8<MODE & ~kModeMulti, T, 4>(sm, stage + (k0 << lw), sg, tl.w0 + k0,
+                                                                              nwk, lw, p, tid, par, rel, true);
                     par ^= 1;
                 }
                 rs = {{0u, 0u}};  // the reduce left the table zero
