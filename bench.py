@@ -15,6 +15,8 @@ Arms and keys of the JSON line:
               the measured HBM copy bandwidth
   cpu_baseline  the CPU oracle on a bounded sample of the same workload (host cores), with its
               single-core throughput beside it
+  write_flagged  the in-place variant that stores only the chunks holding a flagged sample, per
+              variant, with its own bytes rule (never part of value)
   uneven60, twelve60, serve60   the other configurations at N = 1, each in its own sub-object:
               batched throughput and HBM fraction (uneven60, twelve60), and a short serving run
               (chunk latency percentiles, RTF)
@@ -566,6 +568,53 @@ def run_ours(args):
             p.close()
         del f_out
 
+    # the in-place variant that writes back only the changed chunks (RFI_PLAN_WRITE_FLAGGED):
+    # reported beside the headline, never in it. Each call runs on a fresh copy of the input (the
+    # copy is outside the CUDA events around the call); bytes: 1 read + 16 per chunk with a flag
+    # (zero, constant, threshold) or 1 per flagged sample (noise) + 1/8 mask + 12 per window
+    wflag = None
+    if not args.no_write_flagged and args.workload == "gwb60":
+        work = [torch.empty_like(t) for t in dev_in]
+        wcalls = 3
+        per_var = {}
+        tot_ms = tot_bytes = 0.0
+        for v in w.variants:
+            wp = rfi.Plan(8, lens, Ws, v.k, v.mode, v.const, v.seed,
+                          rfi.RFI_PLAN_GRAPH | rfi.RFI_PLAN_AUTOTUNE | rfi.RFI_PLAN_WRITE_FLAGGED, sids)
+            ms = []
+            with torch.cuda.stream(stream):
+                for it in range(1 + wcalls):
+                    for a, b in zip(work, dev_in):
+                        a.copy_(b)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    wp.excise(work, work, masks, counts, stream)
+                    e1.record(stream)
+                    stream.synchronize()
+                    if it:
+                        ms.append(e0.elapsed_time(e1))
+            wst, _ = wp.stats(stream=stream)
+            wp.close()
+            if wst != 0:
+                raise RuntimeError("write-flagged device status %s" % rfi.rfi_status_string(wst))
+            m16 = torch.cat([m.view(torch.int16) for m in masks])
+            if v.mode == workloads.NOISE:
+                written = float(sum(int(c.sum().item()) for c in counts))
+            else:
+                written = 16.0 * float((m16 != 0).sum().item())
+            nbytes = samples_per_call * (1 + 1 / 8) + written + windows_per_call * 12
+            call_ms = max_over_ranks(statistics.mean(ms))
+            per_var[v.name] = {"ms_per_call": round(call_ms, 4), "written_bytes": int(written)}
+            tot_ms += call_ms
+            tot_bytes += nbytes
+        wflag = {"value": sum_over_ranks(samples_per_call * len(w.variants)) / (tot_ms * 1e-3) / 1e9, "unit": UNIT,
+                 "ms_per_step": tot_ms, "calls_per_variant": wcalls, "variants": per_var,
+                 "achieved_gbs": tot_bytes / (tot_ms * 1e-3) / 1e9, "frac": tot_bytes / (tot_ms * 1e-3) / 1e9 / peak,
+                 "bytes_rule": "per sample 1 read + 1/8 mask; 16 B per written chunk (zero, const, clip) or 1 B "
+                               "per flagged sample (noise); per window 4 count + 8 M/D",
+                 "form": "in place, RFI_PLAN_WRITE_FLAGGED (only chunks with a flag are stored); not part of value"}
+        del work
+
     # end to end through rfi_excise_host with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -667,6 +716,7 @@ def run_ours(args):
             "mom": mom,
             "digital_copy": copies,
             "fused_format": fused,
+            "write_flagged": wflag,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "gpu_launches_note": "persistent-kernel and noise_fill launches in the timed region of `value`",
@@ -885,6 +935,7 @@ def make_parser():
     ap.add_argument("--no-mom", action="store_true")
     ap.add_argument("--no-copies", action="store_true")
     ap.add_argument("--no-fused", action="store_true")
+    ap.add_argument("--no-write-flagged", action="store_true")
     ap.add_argument("--no-subs", action="store_true",
                     help="leave out the uneven60, twelve60 and serve60 sub-objects of the gwb60 line")
     ap.add_argument("--sub-steps", type=int, default=10)

@@ -108,6 +108,18 @@ typedef enum { RFI_OUT_SAME = 0, RFI_OUT_F16 = 1, RFI_OUT_BF16 = 2 } rfi_out_for
                                      rfi_plan_destroy frees. Ignored with RFI_PLAN_PER_STREAM,
                                      RFI_PLAN_POWER, fp16/bf16 output, by rfi_excise_host, and in
                                      plans with a stream of 2^31 samples or more */
+#define RFI_PLAN_WRITE_FLAGGED 0x80u /* in-place excision that writes back only what changes:
+                                        rfi_excise requires out[i] == in[i] for every stream
+                                        (RFI_ERR_INVALID_ARG otherwise) and stores only the
+                                        16-byte chunks that hold a flagged sample (zero, constant,
+                                        threshold) or only the flagged samples themselves (digital
+                                        noise); masks and counts are written in full. About 1 + f
+                                        bytes of sample traffic per sample (f the fraction of
+                                        chunks with a flag) instead of 2. 8-bit batched plans with
+                                        per-window MAD only, without RFI_PLAN_POWER, fp16/bf16
+                                        output or digital copies (RFI_ERR_UNSUPPORTED otherwise);
+                                        RFI_PLAN_NOISE_PASS is ignored; rfi_excise_host writes
+                                        every sample as usual */
 #define RFI_PLAN_INJECT_TIMEOUT 0x100u /* test hook: CTA 0 waits on a barrier nothing arrives
                                           on (bounded by 1 ms), latching RFI_ERR_TIMEOUT */
 

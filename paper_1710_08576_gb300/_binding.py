@@ -31,6 +31,7 @@ RFI_PLAN_AUTOTUNE = 0x8
 RFI_PLAN_POWER = 0x10
 RFI_PLAN_NO_SPLIT = 0x20
 RFI_PLAN_NOISE_PASS = 0x40
+RFI_PLAN_WRITE_FLAGGED = 0x80
 RFI_OUT_SAME, RFI_OUT_F16, RFI_OUT_BF16 = 0, 1, 2
 RFI_MAX_COPIES = 8
 RFI_PLAN_INJECT_TIMEOUT = 0x100

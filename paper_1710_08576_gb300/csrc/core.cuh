@@ -927,8 +927,10 @@ __device__ __forceinline__ uint32_t sq4(uint32_t w, uint32_t keep) {
     return static_cast<uint32_t>(__dp4a(v, v, 0));
 }
 
-// rsrc: the shared record r was loaded from (its int8 constants are read from there).
-template <int BITS, int MODE, int T, bool PW, class K, int OUTF = 0>
+// rsrc: the shared record r was loaded from (its int8 constants are read from there). FO (8-bit
+// in-place form): chunks without a flagged sample are not stored, and in noise mode no chunk is
+// (the noise pass writes every flagged sample).
+template <int BITS, int MODE, int T, bool PW, class K, int OUTF = 0, bool FO = false>
 __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, const Rep &r, const K &p,
                                                   int tid, uint32_t *nlc, Pow &pw, const RepShared *rsrc) {
     constexpr int BPS = Geo<BITS>::kBps;
@@ -965,7 +967,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 v.z = rep8_word<MODE>(v.z, k, f2);
                 v.w = rep8_word<MODE>(v.w, k, f3);
                 const uint32_t bits = chunk_bits(f0, f1, f2, f3);
-                store_chunk8<OUTF>(w.out, c, v, true);
+                if (!FO || (MODE != 3 && bits)) store_chunk8<OUTF>(w.out, c, v, true);
                 if (PW) pw.z += sq4(v.x, ~0u) + sq4(v.y, ~0u) + sq4(v.z, ~0u) + sq4(v.w, ~0u);
                 mk[c] = static_cast<uint16_t>(bits);
                 flagged += __popc(bits);
@@ -988,14 +990,15 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                     bits = chunk_bits(f0, f1, f2, f3);
                 }
                 if (c < nfull) {
-                    store_chunk8<OUTF>(w.out, c, v, w.vec);
+                    if (!FO || (MODE != 3 && bits)) store_chunk8<OUTF>(w.out, c, v, w.vec);
                 } else {  // ragged last chunk of the window
                     const int valid = nbytes - c * 16;
                     bits &= (1u << valid) - 1u;
                     const uint32_t ww[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
-                        if (j < valid) store_sample<8, OUTF>(w.out, c * 16 + j, static_cast<int8_t>(ww[j >> 2] >> ((j & 3) * 8)));
+                        if (j < valid && (!FO || (MODE != 3 && ((bits >> j) & 1u))))
+                            store_sample<8, OUTF>(w.out, c * 16 + j, static_cast<int8_t>(ww[j >> 2] >> ((j & 3) * 8)));
                 }
                 if (PW) {
                     // the samples of the window only: the ragged chunk's tail bytes are not its own
@@ -1168,7 +1171,8 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
     Pow pw = {0u, 0u};
     const KeysPre key{p};
     if (!STATS && !COPIES)
-        f = phase_replace<BITS, RMODE, T, PW, KeysPre, OUTF>(sm, w, r, key, tid, &sm.ctl->ncount[par], pw, &sm.ctl->rep);
+        f = phase_replace<BITS, RMODE, T, PW, KeysPre, OUTF, (MODE & kModeFlaggedOnly) != 0>(
+            sm, w, r, key, tid, &sm.ctl->ncount[par], pw, &sm.ctl->rep);
     if (!STATS && !COPIES && RMODE == 3) {
         if (BITS == 8) {
             noise_deferred8<T, PW, KeysPre, OUTF>(sm, w, r, key, tid, f, pw);

@@ -35,6 +35,10 @@ constexpr int kMaxCopies = 8;
 // share one reduce and one set of barriers. A separate instantiation, so that plans without such
 // windows keep the plain kernel's shared-memory layout and code.
 constexpr int kModeMulti = 256;
+// Flag bit of the in-place form that writes back only what changes (RFI_PLAN_WRITE_FLAGGED):
+// chunks without a flagged sample are not stored, and with digital noise no chunk is (the noise
+// pass writes every flagged sample). Its own instantiation, like kModeMulti.
+constexpr int kModeFlaggedOnly = 512;
 
 // One variant of a digital-copy pass.
 struct Variant {

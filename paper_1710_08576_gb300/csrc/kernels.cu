@@ -17,6 +17,9 @@ int persistent_occupancy_mom_b8(int, const Shape &);
 cudaError_t launch_persistent_multi_b8(int, const Shape &, int, const Seg *, const Tile *, int, const Params &,
                                        unsigned *, int, cudaStream_t);
 int persistent_occupancy_multi_b8(int, const Shape &);
+cudaError_t launch_persistent_fo_b8(int, const Shape &, int, const Seg *, const Tile *, int, const Params &,
+                                    unsigned *, int, cudaStream_t);
+int persistent_occupancy_fo_b8(int, const Shape &);
 int persistent_occupancy_mom_b12(int, const Shape &);
 cudaError_t launch_mom_b8(const MomChunk *, int, const int32_t *, int32_t *, int, cudaStream_t);
 cudaError_t launch_mom_b12(const MomChunk *, int, const int32_t *, int32_t *, int, cudaStream_t);
@@ -37,6 +40,7 @@ size_t stream_smem_bytes(int bits, int mode, int consumer_warps, int ncopies, in
 
 int persistent_occupancy(int bits, int mode, const Shape &s) {
     if (mode & kModeMulti) return bits == 8 ? persistent_occupancy_multi_b8(mode, s) : 0;
+    if (mode & kModeFlaggedOnly) return bits == 8 ? persistent_occupancy_fo_b8(mode, s) : 0;
     if (mode >= kModeStats)
         return bits == 8 ? persistent_occupancy_mom_b8(mode, s) : persistent_occupancy_mom_b12(mode, s);
     return bits == 8 ? persistent_occupancy_b8(mode, s) : persistent_occupancy_b12(mode, s);
@@ -46,6 +50,9 @@ cudaError_t launch_persistent(int bits, int mode, const Shape &s, int grid, cons
                               int ntiles, const Params &p, unsigned *counter, int inject, cudaStream_t st) {
     if (mode & kModeMulti)
         return bits == 8 ? launch_persistent_multi_b8(mode, s, grid, segs, tiles, ntiles, p, counter, inject, st)
+                         : cudaErrorInvalidValue;
+    if (mode & kModeFlaggedOnly)
+        return bits == 8 ? launch_persistent_fo_b8(mode, s, grid, segs, tiles, ntiles, p, counter, inject, st)
                          : cudaErrorInvalidValue;
     if (mode >= kModeStats)
         return bits == 8 ? launch_persistent_mom_b8(mode, s, grid, segs, tiles, ntiles, p, counter, inject, st)

@@ -300,6 +300,7 @@ rfi_status plan_check_buffers(const rfi_plan_s *P, const void *const *in, void *
     if (!in || !out) return RFI_ERR_INVALID_ARG;
     for (int i = 0; i < P->S; ++i) {
         if (!in[i] || !out[i]) return RFI_ERR_INVALID_ARG;
+        if (P->write_flagged && in[i] != out[i]) return RFI_ERR_INVALID_ARG;
         if (P->bits == 12 && ((reinterpret_cast<uintptr_t>(in[i]) | reinterpret_cast<uintptr_t>(out[i])) & 1))
             return RFI_ERR_ALIGNMENT;
         if (P->out_format != RFI_OUT_SAME && (reinterpret_cast<uintptr_t>(out[i]) & 1)) return RFI_ERR_ALIGNMENT;
@@ -358,7 +359,8 @@ static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_va
     if (!(d->k > 0.0) || !std::isfinite(d->k) || d->k > 1.0e6) return RFI_ERR_INVALID_ARG;
     if (d->mode < RFI_REPLACE_ZERO || d->mode > RFI_REPLACE_NOISE) return RFI_ERR_INVALID_ARG;
     const uint32_t known = RFI_PLAN_PER_STREAM | RFI_PLAN_BATCHED | RFI_PLAN_GRAPH | RFI_PLAN_AUTOTUNE |
-                           RFI_PLAN_INJECT_TIMEOUT | RFI_PLAN_POWER | RFI_PLAN_NO_SPLIT | RFI_PLAN_NOISE_PASS;
+                           RFI_PLAN_INJECT_TIMEOUT | RFI_PLAN_POWER | RFI_PLAN_NO_SPLIT | RFI_PLAN_NOISE_PASS |
+                           RFI_PLAN_WRITE_FLAGGED;
     if (d->flags & ~known) return RFI_ERR_INVALID_ARG;
     if ((d->flags & RFI_PLAN_PER_STREAM) && (d->flags & (RFI_PLAN_BATCHED | RFI_PLAN_GRAPH)))
         return RFI_ERR_INVALID_ARG;
@@ -368,6 +370,10 @@ static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_va
     if ((d->flags & RFI_PLAN_POWER) && ((d->flags & RFI_PLAN_PER_STREAM) || d->mom_windows >= 2))
         return RFI_ERR_UNSUPPORTED;
     if (d->out_format < RFI_OUT_SAME || d->out_format > RFI_OUT_BF16) return RFI_ERR_INVALID_ARG;
+    if ((d->flags & RFI_PLAN_WRITE_FLAGGED) &&
+        (d->sample_bits != 8 || (d->flags & (RFI_PLAN_PER_STREAM | RFI_PLAN_POWER)) || d->mom_windows >= 2 ||
+         d->out_format != RFI_OUT_SAME || nvar > 0))
+        return RFI_ERR_UNSUPPORTED;
     if (d->out_format != RFI_OUT_SAME &&
         ((d->flags & (RFI_PLAN_PER_STREAM | RFI_PLAN_POWER)) || d->mom_windows >= 2 || nvar > 0 ||
          (d->out_format == RFI_OUT_BF16 && d->sample_bits == 12)))
@@ -426,12 +432,13 @@ static rfi_status plan_create(const rfi_plan_desc *d, int32_t nvar, const rfi_va
     // segments of < 2^31 samples (others keep it in the excision kernel)
     bool short_segs = true;
     for (int i = 0; i < P->S; ++i) short_segs = short_segs && P->len[i] < (int64_t{1} << 31);
+    P->write_flagged = (P->flags & RFI_PLAN_WRITE_FLAGGED) != 0;
     P->fill = (P->flags & RFI_PLAN_NOISE_PASS) && P->mode == RFI_REPLACE_NOISE && !(P->flags & RFI_PLAN_PER_STREAM) &&
-              !P->power && P->ncopy == 0 && P->out_format == RFI_OUT_SAME && short_segs;
+              !P->power && P->ncopy == 0 && P->out_format == RFI_OUT_SAME && short_segs && !P->write_flagged;
     // small windows of 2^l samples: the multi-window form of the 8-bit kernel (several windows
     // per histogram, reduce and set of barriers)
     if (P->bits == 8 && P->ncopy == 0 && !P->power && P->out_format == RFI_OUT_SAME &&
-        !(P->flags & RFI_PLAN_PER_STREAM)) {
+        !(P->flags & RFI_PLAN_PER_STREAM) && !P->write_flagged) {
         for (int i = 0; i < P->S && !P->multi; ++i) {
             const int32_t W = P->W[i];
             P->multi = W >= 512 && W <= 8192 && (W & (W - 1)) == 0 && P->len[i] >= 2 * static_cast<int64_t>(W);

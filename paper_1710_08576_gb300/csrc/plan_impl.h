@@ -57,6 +57,8 @@ struct rfi_plan_s {
     bool power = false;
     // some stream has windows of 2^l samples, 512 <= 2^l <= 8192: the multi-window form
     bool multi = false;
+    // RFI_PLAN_WRITE_FLAGGED: in place, only changed chunks are stored
+    bool write_flagged = false;
     uint64_t *d_pow = nullptr;
     int out_format = RFI_OUT_SAME;  // fused output format
     // digital noise as a second pass (noise_fill): the excision pass replaces with 0, then the
@@ -121,6 +123,7 @@ inline int plan_kernel_mode(const rfi_plan_s *P) {
     const int fmt = P->out_format == RFI_OUT_F16 ? kModeF16 : (P->out_format == RFI_OUT_BF16 ? kModeBF16 : 0);
     if (P->ncopy > 0) return kModeCopies;
     const int m = (P->fill && P->kmom < 2 ? 0 : P->mode) | (P->power ? kModePower : 0) | fmt;
+    if (P->write_flagged) return m | kModeFlaggedOnly;
     return m | (P->multi && m < 4 ? kModeMulti : 0);
 }
 // Kernel mode of the estimation pass of a Median-of-MAD plan.

@@ -162,3 +162,18 @@ def test_mom_arguments_checked_before_cuda():
         d = rfi.RfiPlanDesc(8, 1, lens, wins, None, 3.0, 0, 0, 0, flags, None, kmom)
         assert rfi.LIB.rfi_plan_create(ctypes.byref(d), ctypes.byref(h)) == want
     assert rfi.LIB.rfi_stats_mom(None, None, None) == rfi.RFI_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("kw", [
+    dict(bits=12), dict(flags=rfi.RFI_PLAN_PER_STREAM), dict(flags=rfi.RFI_PLAN_POWER), dict(mom_windows=16),
+    dict(out_format=rfi.RFI_OUT_F16),
+])
+def test_write_flagged_unsupported_combinations_fail_before_cuda(kw):
+    """The in-place form that writes back only changed chunks is 8-bit, batched, per-window MAD,
+    without power metering or a fused output format."""
+    args = dict(bits=8, stream_len=[4096], window_len=[1024], k=3.0, mode=0)
+    flags = rfi.RFI_PLAN_WRITE_FLAGGED | kw.get("flags", 0)
+    d = rfi.make_desc(kw.get("bits", 8), args["stream_len"], args["window_len"], args["k"], args["mode"],
+                      flags=flags, mom_windows=kw.get("mom_windows", 0), out_format=kw.get("out_format", 0))
+    st, h = rfi.rfi_plan_create(d)
+    assert st == rfi.RFI_ERR_UNSUPPORTED and h is None
