@@ -34,6 +34,12 @@
 // the flagged samples' positions into a per-group list, and after one more group barrier all
 // threads evaluate Philox for the list; a window whose list would overflow hands the rest of
 // its flagged samples to a per-warp path that numbers them across the warp.
+//
+// Small int8 windows (2^l = 512..8192 samples) can go several to a table (process_tile_multi8):
+// window slot g of a tile is counted by its own group of lanes, so up to eight windows share one
+// reduce, one set of barriers and searches on separate warps. The in-place form that writes
+// back only what changes skips the stores of chunks without a flagged sample (phase_replace's
+// FO parameter).
 
 #pragma once
 
