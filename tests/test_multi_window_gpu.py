@@ -1,10 +1,11 @@
 """The multi-window form of the int8 kernel against the CPU oracle, bit for bit.
 
-Plans with windows of 2^l = 512..8192 samples run the instantiation that histograms up to four
-windows of a tile at once (window slot g in lanes 8g..8g+7 of the lane-striped table), reduces
-them in one pass that also clears the table, and searches them on warps 0..3 in parallel. These
-cases pin down what that adds to the per-window path: tiles of every remainder of four windows
-(sub-tiles of 1, 2 and 3 windows), the switch between multi-window tiles and per-window tiles
+Plans with windows of 2^l = 512..8192 samples run the instantiation that histograms several
+windows of a tile at once in the lane-striped table: eight for windows of at most 2048 samples
+(window slot g in lanes 4g..4g+3), four for 4096 and 8192 (lanes 8g..8g+7). It reduces them in
+one pass that also clears the table and searches them on several warps in parallel. These cases
+pin down what that adds to the per-window path: tiles of every remainder of the slot count
+(sub-tiles of 1 to 7 windows), the switch between multi-window tiles and per-window tiles
 (16384-sample windows, ragged tails, windows that are not a power of two, unaligned buffers) in
 one kernel, whose table then has to be cleared or its running sums reset, every replacement
 mode, both noise forms and every consumer-group size.
@@ -28,8 +29,8 @@ def _streams(lens, seed, burst_rate=4e-3):
 @pytest.mark.parametrize("cw", [4, 8, 16])
 def test_every_tile_remainder(cuda, rfi, W, cw):
     """16 KiB stages hold 16384 / W windows; streams of 1 .. 16384 / W + 5 full windows (and one
-    ragged tail each) make tiles of every size, so the last sub-tile of four holds 1, 2 or 3
-    windows, and a tail window takes the per-window path right after."""
+    ragged tail each) make tiles of every size, so the last sub-tile holds fewer windows than
+    there are slots, and a tail window takes the per-window path right after."""
     per = 16384 // W
     counts = sorted(set([1, 2, 3, 4, 5, 6, 7, per, per + 1, per + 3, per + 5]))
     lens = [n * W for n in counts] + [n * W + 77 for n in counts[:4]]
