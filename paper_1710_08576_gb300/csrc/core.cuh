@@ -28,9 +28,10 @@
 //
 // Digital-noise replacement is deferred and shared out over the group, in one of two ways
 // chosen by sample width for the flag densities each one serves best. int8 (sparse, bursty
-// flags): the replace pass keeps every chunk's flag mask in shared memory; a block scan of
-// the threads' flag counts numbers the flagged samples and each thread evaluates Philox for
-// every T-th of them, found by a binary search. 12-bit (dense flags): the replace pass writes
+// flags): the replace pass lists the chunks that hold a flagged sample with their flag masks;
+// after a group barrier the warps share out the list two chunks at a time, expand each mask
+// over a half-warp into a per-warp queue of positions, and evaluate Philox whenever 32 are
+// queued, so every lane of a batch has a sample. 12-bit (dense flags): the replace pass writes
 // the flagged samples' positions into a per-group list, and after one more group barrier all
 // threads evaluate Philox for the list; a window whose list would overflow hands the rest of
 // its flagged samples to a per-warp path that numbers them across the warp.
@@ -297,8 +298,9 @@ struct Shm {
     int ncopies;         // 12-bit only
     int bar_id;          // named barrier of this consumer group
     CopyShared *cp;      // digital copy: per-variant state (or null)
-    uint16_t *nlist;     // digital noise work area (or null): int8, the window's chunk flag masks;
-                         // 12-bit, the positions of its flagged samples
+    uint16_t *nlist;     // digital noise work area (or null): int8, the entries of the chunks that
+                         // hold flagged samples (32-bit); 12-bit, the positions of flagged samples
+    uint32_t *nring;     // int8 digital noise: kNoiseRing positions per consumer warp (or null)
     ApplyTile *at;       // apply passes: the current tile's thresholds and counts (or null)
     struct MultiTile *mt;  // 8-bit, one group: state of a multi-window tile (or null)
 };
@@ -308,6 +310,9 @@ struct Shm {
 // the per-warp path.
 constexpr int kNoiseList = 4096;
 constexpr uint16_t kNoiseSkip = 0xFFFFu;
+// Positions a warp's ring holds: fewer than 32 wait between two batches, and one expansion step
+// adds at most 32.
+constexpr int kNoiseRing = 64;
 
 // Per-thread sums of x^2 and z^2 of the power-metered excision. A thread sees at most
 // 65536 / 128 samples of a window, each below 2^22, so 32 bits hold its sums.
@@ -885,46 +890,74 @@ __device__ __forceinline__ void noise_list(const Shm &sm, const Win &w, const Re
     }
 }
 
-// Digital noise (int8), after the replace pass: thread t has flagged cnt samples in its chunks
-// t, t + T, t + 2T, ... whose masks are in sm.nlist. A block scan gives each thread its first
-// index, so the window's flagged samples are numbered in the order (owner thread, chunk, bit);
-// thread t takes numbers t, t + T, ..., finds each one's owner by a binary search over the
-// first indices (16-bit values in the now idle cumulative-count array: a thread that owns a
-// flagged sample starts below 65536), walks the owner's chunks to the sample and evaluates
-// Philox for it. Every walk is bounded by the window and every store is checked against the
-// window's length.
+// Digital noise (int8), replace pass: the warp appends one list entry per chunk of its round
+// that holds a flagged sample, (chunk << 16) | the chunk's 16 flag bits, at places reserved
+// with one shared atomic on the entry count *nlc. The list has room for every chunk of a stage.
+// Called by all lanes of the warp (bits = 0 for a lane without a chunk).
+__device__ __forceinline__ void noise_note8(const Shm &sm, int lane, int c, uint32_t bits, uint32_t *nlc) {
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bits != 0u);
+    if (bal == 0u) return;
+    uint32_t base = 0u;
+    if (lane == 0) base = atomicAdd(nlc, static_cast<uint32_t>(__popc(bal)));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (bits)
+        reinterpret_cast<uint32_t *>(sm.nlist)[base + __popc(bal & ((1u << lane) - 1u))] =
+            (static_cast<uint32_t>(c) << 16) | bits;
+}
+
+// Digital noise (int8), after the replace pass and a group barrier: the n entries noted by
+// noise_note8, in any order (a sample's noise depends only on its absolute index). Warp w
+// expands entries 2w and 2w + 1, then 2w + 2NW and 2w + 2NW + 1, and so on: each half-warp
+// takes one entry and its lane j tests flag bit j. The flagged positions go into the warp's
+// ring, compacted by a ballot and a prefix popcount, and whenever 32 are waiting every lane
+// takes one and emit(pos) evaluates and stores its noise. Fewer than 32 are left for the end.
+// Every lane does Philox work in every batch but the last, however the flags are spread over
+// the chunks, and the chunks are shared out evenly between the warps.
+template <int T, class Emit>
+__device__ __forceinline__ void noise_expand8(const Shm &sm, uint32_t n, int tid, Emit &&emit) {
+    constexpr uint32_t NW = T / 32;
+    constexpr uint32_t RM = kNoiseRing - 1;
+    const int lane = tid & 31;
+    const uint32_t warp = static_cast<uint32_t>(tid >> 5);
+    const uint32_t *list = reinterpret_cast<const uint32_t *>(sm.nlist);
+    uint32_t *ring = sm.nring + warp * kNoiseRing;
+    const uint32_t j = static_cast<uint32_t>(lane & 15);
+    const uint32_t below = (1u << lane) - 1u;
+    uint32_t head = 0u, tail = 0u;  // positions taken / queued so far (tail - head < 32 between steps)
+    for (uint32_t e0 = 2u * warp; e0 < n; e0 += 2u * NW) {
+        const uint32_t e = e0 + static_cast<uint32_t>(lane >> 4);
+        const uint32_t ent = e < n ? list[e] : 0u;
+        const bool fl = ((ent >> j) & 1u) != 0u;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, fl);
+        if (fl) ring[(tail + static_cast<uint32_t>(__popc(bal & below))) & RM] = (ent >> 16) * 16u + j;
+        tail += static_cast<uint32_t>(__popc(bal));
+        if (tail - head >= 32u) {
+            __syncwarp();
+            const uint32_t pos = ring[(head + static_cast<uint32_t>(lane)) & RM];
+            __syncwarp();  // read before the next step refills the slot
+            head += 32u;
+            emit(pos);
+        }
+    }
+    if (tail != head) {
+        __syncwarp();
+        if (static_cast<uint32_t>(lane) < tail - head) emit(ring[(head + static_cast<uint32_t>(lane)) & RM]);
+    }
+}
+
+// Digital noise (int8) of one window, after its replace pass noted its chunks in the list (*nlc
+// entries): one group barrier, then noise_expand8. Every store is checked against the window's
+// length.
 template <int T, bool PW, class K, int OUTF = 0>
 __device__ __forceinline__ void noise_deferred8(const Shm &sm, const Win &w, const Rep &r, const K &p, int tid,
-                                                uint32_t cnt, Pow &pw) {
-    constexpr int NW = T / 32;
-    const uint32_t first = block_offsets<T>(sm, cnt, tid);  // group barrier inside
-    uint32_t total = 0;
-#pragma unroll
-    for (int i = 0; i < NW; ++i) total += sm.ctl->warp_tot[i];
-    uint16_t *firsts = reinterpret_cast<uint16_t *>(sm.cum);
-    firsts[tid] = static_cast<uint16_t>(first < 65535u ? first : 65535u);
-    named_bar(sm.bar_id, T);
-    const int nchunks = (w.n + 15) >> 4;
-    for (uint32_t q = static_cast<uint32_t>(tid); q < total; q += T) {
-        int u = 0;
-#pragma unroll
-        for (int step = T / 2; step >= 1; step >>= 1)
-            if (firsts[u + step] <= q) u += step;
-        uint32_t j = q - firsts[u];
-        int c = u;
-        uint32_t b = sm.nlist[c];
-        while (j >= static_cast<uint32_t>(__popc(b)) && c + T < nchunks) {
-            j -= __popc(b);
-            c += T;
-            b = sm.nlist[c];
-        }
-        if (j >= static_cast<uint32_t>(__popc(b))) continue;
-        const int pos = c * 16 + nth_set_bit(b, static_cast<int>(j));
-        if (pos >= w.n) continue;
+                                                const uint32_t *nlc, Pow &pw) {
+    named_bar(sm.bar_id, T);  // every entry of the window is in the list
+    noise_expand8<T>(sm, *nlc, tid, [&](uint32_t pos) {
+        if (pos >= static_cast<uint32_t>(w.n)) return;
         const int32_t z = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pos, Geo<8>::kLo, Geo<8>::kHi);
-        store_sample<8, OUTF>(w.out, pos, z);
+        store_sample<8, OUTF>(w.out, static_cast<int>(pos), z);
         if (PW) pw.z += static_cast<uint32_t>(z * z);
-    }
+    });
 }
 
 // Sum of squares of the bytes of w kept by keep (0xFF per kept byte), as signed int8 samples.
@@ -977,7 +1010,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 if (PW) pw.z += sq4(v.x, ~0u) + sq4(v.y, ~0u) + sq4(v.z, ~0u) + sq4(v.w, ~0u);
                 mk[c] = static_cast<uint16_t>(bits);
                 flagged += __popc(bits);
-                if (MODE == 3) sm.nlist[c] = static_cast<uint16_t>(bits);
+                if (MODE == 3) noise_note8(sm, lane, c, bits, nlc);
             }
         }
         // warp-uniform rounds: lane handles chunk base + lane
@@ -1020,8 +1053,8 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 }
                 flagged += __popc(bits);
                 if (mk) mk[c] = static_cast<uint16_t>(bits);
-                if (MODE == 3) sm.nlist[c] = static_cast<uint16_t>(bits);
             }
+            if (MODE == 3) noise_note8(sm, lane, c, bits, nlc);
         }
         if (mk) {
             for (int c = nchunks + tid; c < 2 * w.mask_words; c += T) mk[c] = 0;
@@ -1181,7 +1214,7 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
             sm, w, r, key, tid, &sm.ctl->ncount[par], pw, &sm.ctl->rep);
     if (!STATS && !COPIES && RMODE == 3) {
         if (BITS == 8) {
-            noise_deferred8<T, PW, KeysPre, OUTF>(sm, w, r, key, tid, f, pw);
+            noise_deferred8<T, PW, KeysPre, OUTF>(sm, w, r, key, tid, &sm.ctl->ncount[par], pw);
         } else {
             named_bar(sm.bar_id, T);  // every flagged position of the window is in the list
             noise_list<BITS, T, PW, KeysPre, OUTF>(sm, w, r, key, tid, &sm.ctl->ncount[par], pw);
@@ -1212,7 +1245,7 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
                 default:
                     fv = phase_replace<BITS, 3, T, false>(sm, wv, rv, vkey, tid, nc, pw, &sm.cp->vrep[v]);
                     if (BITS == 8) {
-                        noise_deferred8<T, false>(sm, wv, rv, vkey, tid, fv, pw);
+                        noise_deferred8<T, false>(sm, wv, rv, vkey, tid, nc, pw);
                     } else {
                         named_bar(sm.bar_id, T);
                         noise_list<BITS, T, false>(sm, wv, rv, vkey, tid, nc, pw);
@@ -1245,7 +1278,7 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
             __threadfence_block();
             const uint32_t cnt = atomicExch(&sm.ctl->count[par], 0u);
             sm.ctl->done[par] = 0u;
-            if (BITS == 12 && RMODE == 3) sm.ctl->ncount[par] = 0u;  // every warp has read it
+            if (RMODE == 3 && !COPIES) sm.ctl->ncount[par] = 0u;  // every warp has read it
             if (COPIES) {
                 for (int v = 0; v < params_nvar(p); ++v) {
                     const uint32_t cv = atomicExch(&sm.cp->vcount[v][par], 0u);
@@ -1278,8 +1311,8 @@ __device__ bool process_window(const Shm &sm, const Win &w, const Seg &sg, int64
 // Eq. 1 and Eq. 2 over a whole tile of nw full int8 windows of one segment, W = 2^lw samples
 // each, 16-byte aligned, window k (of the tile) with the thresholds reps[k] already in shared
 // memory: the replace pass over all of the tile's chunks (a warp's round of 32 chunks lies in
-// one window, whose flag count takes one shared atomic), then the digital noise numbered over
-// the tile as in noise_deferred8, each sample taking its window's M and spread. The last warp
+// one window, whose flag count takes one shared atomic), then the digital noise of the listed
+// chunks as in noise_deferred8, each sample taking its window's M and spread. The last warp
 // writes the windows' counts from cnt (and zeroes them) and, when release_bar != 0, releases
 // the stage. Windows start at window w0 of the segment.
 template <int RMODE, int T>
@@ -1294,7 +1327,6 @@ __device__ void replace_tile8(const Shm &sm, const uint8_t *stage, const Seg &sg
     uint8_t *out = sg.out + (static_cast<int64_t>(w0) << lw);
     uint16_t *mk = sg.mask ? reinterpret_cast<uint16_t *>(sg.mask + static_cast<int64_t>(w0) * sg.mask_words)
                            : nullptr;
-    uint32_t own = 0;  // this thread's flagged samples (noise numbering)
     for (int c0 = warp * 32; c0 < nchunks; c0 += T) {
         const int k = c0 >> lcw;
         const RepShared &rk = reps[k];
@@ -1323,42 +1355,20 @@ __device__ void replace_tile8(const Shm &sm, const uint8_t *stage, const Seg &sg
         }
         store_chunk8<0>(out, c, v, true);
         if (mk) mk[c] = static_cast<uint16_t>(bits);
-        if (RMODE == 3) sm.nlist[c] = static_cast<uint16_t>(bits);
-        own += __popc(bits);
+        if (RMODE == 3) noise_note8(sm, lane, c, bits, &sm.ctl->ncount[par]);
         const uint32_t wf = __reduce_add_sync(0xFFFFFFFFu, __popc(bits));
         if (lane == 0 && wf) atomicAdd(&cnt[k], wf);
     }
 
     if (RMODE == 3) {
-        // number the tile's flagged samples by (owner thread, chunk, bit), as noise_deferred8
-        const uint32_t first = block_offsets<T>(sm, own, tid);  // group barrier inside
-        uint32_t total = 0;
-#pragma unroll
-        for (int i = 0; i < NW; ++i) total += sm.ctl->warp_tot[i];
-        uint16_t *firsts = reinterpret_cast<uint16_t *>(sm.cum);
-        firsts[tid] = static_cast<uint16_t>(first < 65535u ? first : 65535u);
-        named_bar(sm.bar_id, T);
+        named_bar(sm.bar_id, T);  // every entry of the tile is in the list
         const KeysPre key{p};
         const int64_t abs0 = sg.abs0 + (static_cast<int64_t>(w0) << lw);
-        for (uint32_t q = static_cast<uint32_t>(tid); q < total; q += T) {
-            int u = 0;
-#pragma unroll
-            for (int step = T / 2; step >= 1; step >>= 1)
-                if (firsts[u + step] <= q) u += step;
-            uint32_t j = q - firsts[u];
-            int c = u;
-            uint32_t b = sm.nlist[c];
-            while (j >= static_cast<uint32_t>(__popc(b)) && c + T < nchunks) {
-                j -= __popc(b);
-                c += T;
-                b = sm.nlist[c];
-            }
-            if (j >= static_cast<uint32_t>(__popc(b))) continue;
-            const int pos = c * 16 + nth_set_bit(b, static_cast<int>(j));
+        noise_expand8<T>(sm, sm.ctl->ncount[par], tid, [&](uint32_t pos) {
             const RepShared &rk = reps[pos >> lw];
             const int32_t z = noise_value(rk.M, rk.sigq, key, sg.stream_id, abs0 + pos, Geo<8>::kLo, Geo<8>::kHi);
             out[pos] = static_cast<uint8_t>(z);
-        }
+        });
     }
 
     if (lane == 0) {
@@ -1367,6 +1377,7 @@ __device__ void replace_tile8(const Shm &sm, const uint8_t *stage, const Seg &sg
             // last warp of the tile: every count is in and every read of the stage is done
             __threadfence_block();
             sm.ctl->done[par] = 0u;
+            if (RMODE == 3) sm.ctl->ncount[par] = 0u;  // every warp has read it
             unsigned long long tot = 0ull;
             for (int k = 0; k < nw; ++k) {
                 const uint32_t ck = cnt[k];

@@ -32,7 +32,8 @@ struct Layout {
     int grp;        // first group block
     int grp_size;   // bytes per group block
     int cum, ctl, bar, meta;  // offsets inside a group block
-    int nlist;                // digital-noise position list inside a group block (0: none)
+    int nlist;                // digital-noise work area inside a group block (0: none)
+    int nring;                // int8 digital noise: the warps' position rings (0: none)
     int amd;                  // apply passes: per stage, {M, dispersion} of its windows (0: none)
     int atile;                // apply passes: thresholds and counts of the current tile (0: none)
     int cps;                  // digital copy: per-variant state inside a group block (0: none)
@@ -55,9 +56,15 @@ __host__ __device__ inline Layout layout(int ncopies, int stages, int stage_byte
     const int meta_end = align_up(L.meta + kMaxStages * static_cast<int>(sizeof(StageMeta)), 128);
     const bool noise = ((mode & 3) == 3 || (mode & kModeCopies) != 0) && (mode & kModeStats) == 0;
     L.nlist = noise ? meta_end : 0;
-    // int8: one 16-bit mask per 16-byte chunk of the largest window (at most a stage); 12-bit:
-    // the position list
-    const int noise_bytes = BITS == 8 ? align_up(stage_bytes / 8 > 128 ? stage_bytes / 8 : 128, 128) : kNoiseList * 2;
+    // int8: a 32-bit entry for every 16-byte chunk of a stage that may hold a flagged sample,
+    // then each consumer warp's ring of kNoiseRing 32-bit positions (multi-window tiles keep the
+    // rings in their cumulative-count area, which is idle by then and large enough); 12-bit: the
+    // position list
+    const int list_bytes = align_up(stage_bytes / 4 > 128 ? stage_bytes / 4 : 128, 128);
+    const int ring_bytes = multi ? 0 : cw * kNoiseRing * 4;
+    static_assert(kNoiseRing * 4 * 16 <= Geo<8>::kCumWords * 2 * kMultiMax, "rings of 16 warps fit the multi-window counts");
+    const int noise_bytes = BITS == 8 ? list_bytes + ring_bytes : kNoiseList * 2;
+    L.nring = (noise && BITS == 8) ? (multi ? L.cum : meta_end + list_bytes) : 0;
     const int list_end = noise ? align_up(meta_end + noise_bytes, 128) : meta_end;
     const bool apply = (mode & kModeApply) != 0;
     L.amd = apply ? list_end : 0;
@@ -86,6 +93,7 @@ __device__ __forceinline__ Shm group_view(uint8_t *smem, const Layout &L, int g,
     sm.ncopies = ncopies;
     sm.bar_id = 1 + g;
     sm.nlist = L.nlist ? reinterpret_cast<uint16_t *>(gb + L.nlist) : nullptr;
+    sm.nring = L.nlist && BITS == 8 ? reinterpret_cast<uint32_t *>(gb + L.nring) : nullptr;
     sm.cp = L.cps ? reinterpret_cast<CopyShared *>(gb + L.cps) : nullptr;
     sm.at = L.atile ? reinterpret_cast<ApplyTile *>(gb + L.atile) : nullptr;
     sm.mt = L.mt ? reinterpret_cast<MultiTile *>(gb + L.mt) : nullptr;
