@@ -4,15 +4,20 @@
 // pass: it writes 0 at every flagged sample, the flag mask and every window's M and D. This
 // kernel then overwrites the flagged samples with M + the Philox noise of spread 1.4826·D, keyed
 // by the absolute sample index as always, so the result is the same bits as the one-pass form.
-// Inside the excision kernel the flagged samples are found and shared out between the window's
-// warps around its barriers, a fixed cost per window; here every warp works on its own block of
-// the mask at full occupancy, with idle lanes where a block holds few flags.
 //
-// Work: segment s covers blocks [fblk[s], fblk[s + 1]) of kFillBlockWords = 64 mask words
-// (2048 samples; a window's mask words are consecutive, windows follow one another). Lane l of
-// a warp holds words 2l and 2l + 1 of its block; the warp numbers the block's flagged samples
-// with a shuffle scan and evaluates Philox for 32 of them at a time, each lane finding its
-// sample's owner lane by a shuffle binary search and the bit by a popcount search.
+// Work: every 128 mask words of a window (4096 samples, fewer at a window's end) are a unit;
+// warp g of the grid takes units g, g + nwarps, ... (segment s holds units [fwin[s], fwin[s + 1]),
+// its windows in order, ceil(mask words / 128) units each). A unit of a window whose count is 0
+// is skipped. Lane l reads the unit's words 4l .. 4l + 3, and the warp moves their flagged
+// samples into its ring of positions:
+//  - a word with at least kFillDense flags goes whole: lane j tests bit j and a ballot with a
+//    prefix popcount gives each flagged lane its place in the ring;
+//  - from the other words every lane gives up one flag per step (its lowest remaining one),
+//    compacted the same way.
+// Whenever 32 positions wait in the ring, every lane takes one and evaluates its noise. A ring
+// entry carries the window's M and D with the position, so the ring runs on across the warp's
+// units of a segment and its last fewer-than-32 positions go out only when the segment changes
+// or the warp ends. Every lane of a batch but those of such a last one has a sample.
 
 #include "core.cuh"
 
@@ -20,7 +25,8 @@ namespace rfi {
 namespace dev {
 
 constexpr int kFillThreads = 256;
-static_assert(kFillBlockWords == 64, "two mask words per lane");
+constexpr int kFillRing = 64;   // positions a warp's ring holds: fewer than 32 wait between steps
+constexpr int kFillDense = 8;   // flags from which a mask word is expanded whole
 
 template <int BITS>
 __device__ __forceinline__ void fill_store(uint8_t *out, uint32_t pos, int32_t z) {
@@ -28,104 +34,117 @@ __device__ __forceinline__ void fill_store(uint8_t *out, uint32_t pos, int32_t z
     else reinterpret_cast<int16_t *>(out)[pos] = static_cast<int16_t>(z);
 }
 
+// The warp's ring: queued positions (segment-relative sample index, with the window's M in the
+// low and D in the high 16 bits of md) and the batches that empty it.
+template <int BITS>
+struct FillRing {
+    uint2 *q;
+    uint32_t head, tail;  // positions taken / queued so far
+    const Seg *g;
+    const KeysPre *key;
+    int lane;
+
+    __device__ __forceinline__ void emit(uint2 e) const {
+        const int32_t M = static_cast<int16_t>(e.y & 0xFFFFu);
+        const uint32_t sigq = 97164u * (e.y >> 16);
+        const int32_t z = noise_value(M, sigq, *key, g->stream_id, g->abs0 + static_cast<int64_t>(e.x),
+                                      Geo<BITS>::kLo, Geo<BITS>::kHi);
+        fill_store<BITS>(g->out, e.x, z);
+    }
+    // Queue the flagged lanes' positions (every lane calls this), then empty a full batch.
+    __device__ __forceinline__ void put(bool fl, uint32_t pos, uint32_t md) {
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, fl);
+        if (fl) q[(tail + static_cast<uint32_t>(__popc(bal & ((1u << lane) - 1u)))) & (kFillRing - 1)] = make_uint2(pos, md);
+        tail += static_cast<uint32_t>(__popc(bal));
+        if (tail - head >= 32u) {
+            __syncwarp();
+            const uint2 e = q[(head + static_cast<uint32_t>(lane)) & (kFillRing - 1)];
+            __syncwarp();  // read before the next step refills the slot
+            head += 32u;
+            emit(e);
+        }
+    }
+    // The positions still waiting (fewer than 32).
+    __device__ __forceinline__ void drain() {
+        if (tail == head) return;
+        __syncwarp();
+        if (static_cast<uint32_t>(lane) < tail - head) emit(q[(head + static_cast<uint32_t>(lane)) & (kFillRing - 1)]);
+        __syncwarp();
+        head = tail;
+    }
+};
+
 // Segments hold fewer than 2^31 samples (the plan routes longer ones through the one-pass form),
-// so every index below fits 32 bits.
+// so every segment-relative index below fits 32 bits.
 template <int BITS>
 __global__ void __launch_bounds__(kFillThreads) noise_fill_kernel(const Seg *__restrict__ segs, int nseg,
-                                                                 const uint32_t *__restrict__ fblk, uint32_t nblk,
+                                                                 const uint32_t *__restrict__ fwin, uint32_t nunits,
                                                                  Params p) {
-    constexpr unsigned kAll = 0xFFFFFFFFu;
+    __shared__ uint2 ring_s[kFillThreads / 32][kFillRing];
     const int lane = threadIdx.x & 31;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const KeysPre key{p};
+    FillRing<BITS> R{ring_s[threadIdx.x >> 5], 0u, 0u, segs, &key, lane};
     int s = 0;
-    for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nblk; b += nwarps) {
-        while (s + 1 < nseg && fblk[s + 1] <= b) ++s;  // a warp's blocks ascend
-        const Seg &g = segs[s];
-        const uint32_t mw = static_cast<uint32_t>(g.mask_words), W = static_cast<uint32_t>(g.W);
-        const uint32_t len = static_cast<uint32_t>(g.len);
-        const uint32_t nwords = ((len + W - 1) / W) * mw;
-        const uint32_t word0 = (b - fblk[s]) * static_cast<uint32_t>(kFillBlockWords);
-        const uint32_t wa = word0 + 2u * static_cast<uint32_t>(lane);
-        const uint32_t ma = wa < nwords ? g.mask[wa] : 0u;
-        const uint32_t mb = wa + 1u < nwords ? g.mask[wa + 1u] : 0u;
-        if (!__any_sync(kAll, (ma | mb) != 0u)) continue;
-        const uint32_t cnt = __popc(ma) + __popc(mb);
-        uint32_t inc = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kAll, inc, o);
-            if (lane >= o) inc += y;
+    for (uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nwarps) {
+        if (fwin[s + 1] <= u) {  // a warp's units ascend: the queue belongs to the segment
+            R.drain();
+            while (s + 1 < nseg && fwin[s + 1] <= u) ++s;
+            R.g = &segs[s];
         }
-        const uint32_t total = __shfl_sync(kAll, inc, 31);
-        const uint32_t excl = inc - cnt;
-        if (W % 32u == 0u && mw % 64u == 0u) {
-            // the block lies in one window k, and sample = 32 * word + bit
-            const uint32_t k = word0 / mw;
-            const int32_t M = g.med[k];
-            const uint32_t S = 97164u * static_cast<uint32_t>(g.mad[k]);
-            for (uint32_t q0 = 0; q0 < total; q0 += 32) {
-                const uint32_t q = q0 + static_cast<uint32_t>(lane);
-                // owner: the last lane whose first number is <= q (lanes without flags share
-                // the next lane's first number, so the search passes over them)
-                int L = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const uint32_t e = __shfl_sync(kAll, excl, L + step);
-                    if (e <= q) L += step;
-                }
-                const uint32_t eL = __shfl_sync(kAll, excl, L);
-                const uint32_t aL = __shfl_sync(kAll, ma, L), bL = __shfl_sync(kAll, mb, L);
-                if (q < total) {
-                    const uint32_t j = q - eL, ca = __popc(aL);
-                    const bool first = j < ca;
-                    const uint32_t bit = static_cast<uint32_t>(nth_set_bit(first ? aL : bL, static_cast<int>(first ? j : j - ca)));
-                    const uint32_t pos = 32u * (word0 + 2u * static_cast<uint32_t>(L) + (first ? 0u : 1u)) + bit;
-                    if (pos < len) {
-                        const int32_t z = noise_value(M, S, key, g.stream_id, g.abs0 + static_cast<int64_t>(pos),
-                                                      Geo<BITS>::kLo, Geo<BITS>::kHi);
-                        fill_store<BITS>(g.out, pos, z);
-                    }
-                }
-            }
+        const Seg &g = segs[s];
+        const uint32_t mw = static_cast<uint32_t>(g.mask_words);
+        const uint32_t upw = (mw + 127u) >> 7;  // units per window
+        const uint32_t local = u - fwin[s];
+        const uint32_t k = local / upw;
+        const uint32_t j0 = (local - k * upw) << 7;
+        if (g.counts && g.counts[k] == 0u) continue;
+        const uint32_t md = (static_cast<uint32_t>(g.med[k]) & 0xFFFFu) | (static_cast<uint32_t>(g.mad[k]) << 16);
+        const uint32_t pos0 = k * static_cast<uint32_t>(g.W);
+        const uint32_t *mk = g.mask + static_cast<size_t>(k) * mw;
+        const uint32_t jl = j0 + 4u * static_cast<uint32_t>(lane);  // this lane's first word
+        uint32_t m[4];
+        if ((mw & 3u) == 0u && (reinterpret_cast<uintptr_t>(mk) & 15u) == 0u) {
+            const uint4 a = jl < mw ? *reinterpret_cast<const uint4 *>(mk + jl) : make_uint4(0u, 0u, 0u, 0u);
+            m[0] = a.x;
+            m[1] = a.y;
+            m[2] = a.z;
+            m[3] = a.w;
         } else {
-            // general windows: each lane brings the window, M, spread and first sample of its
-            // two words (a window's last word holds W mod 32 samples when 32 does not divide W)
-            const uint32_t ka = wa / mw;
-            const uint32_t kb = ka + ((wa + 1u - ka * mw) == mw ? 1u : 0u);
-            const uint32_t sa = ka * W + (wa - ka * mw) * 32u;
-            const uint32_t sb = kb * W + (wa + 1u - kb * mw) * 32u;
-            const bool la = ma != 0u, lb = mb != 0u;
-            const int32_t Ma = la ? g.med[ka] : 0, Mb = lb ? g.med[kb] : 0;
-            const uint32_t Sa = la ? 97164u * static_cast<uint32_t>(g.mad[ka]) : 0u;
-            const uint32_t Sb = lb ? 97164u * static_cast<uint32_t>(g.mad[kb]) : 0u;
-            for (uint32_t q0 = 0; q0 < total; q0 += 32) {
-                const uint32_t q = q0 + static_cast<uint32_t>(lane);
-                int L = 0;
 #pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const uint32_t e = __shfl_sync(kAll, excl, L + step);
-                    if (e <= q) L += step;
-                }
-                const uint32_t eL = __shfl_sync(kAll, excl, L);
-                const uint32_t aL = __shfl_sync(kAll, ma, L), bL = __shfl_sync(kAll, mb, L);
-                const int32_t MaL = __shfl_sync(kAll, Ma, L), MbL = __shfl_sync(kAll, Mb, L);
-                const uint32_t SaL = __shfl_sync(kAll, Sa, L), SbL = __shfl_sync(kAll, Sb, L);
-                const uint32_t saL = __shfl_sync(kAll, sa, L), sbL = __shfl_sync(kAll, sb, L);
-                if (q < total) {
-                    const uint32_t j = q - eL, ca = __popc(aL);
-                    const bool first = j < ca;
-                    const uint32_t bit = static_cast<uint32_t>(nth_set_bit(first ? aL : bL, static_cast<int>(first ? j : j - ca)));
-                    const uint32_t pos = (first ? saL : sbL) + bit;
-                    if (pos < len) {
-                        const int32_t z = noise_value(first ? MaL : MbL, first ? SaL : SbL, key, g.stream_id,
-                                                      g.abs0 + static_cast<int64_t>(pos), Geo<BITS>::kLo, Geo<BITS>::kHi);
-                        fill_store<BITS>(g.out, pos, z);
-                    }
-                }
+            for (int i = 0; i < 4; ++i) m[i] = jl + i < mw ? mk[jl + i] : 0u;
+        }
+        if (!__any_sync(0xFFFFFFFFu, (m[0] | m[1] | m[2] | m[3]) != 0u)) continue;
+        // dense words, one at a time over the whole warp
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t wi = m[i];
+            const bool d = __popc(wi) >= kFillDense;
+            uint32_t dense = __ballot_sync(0xFFFFFFFFu, d);
+            if (d) m[i] = 0u;
+            while (dense) {
+                const int src = __ffs(dense) - 1;
+                dense &= dense - 1u;
+                const uint32_t w = __shfl_sync(0xFFFFFFFFu, wi, src);
+                const uint32_t pos = pos0 + 32u * (j0 + 4u * static_cast<uint32_t>(src) + i) + static_cast<uint32_t>(lane);
+                R.put(((w >> lane) & 1u) != 0u, pos, md);
             }
+        }
+        // the other words: each lane gives up its lowest remaining flag per step
+        while (__any_sync(0xFFFFFFFFu, (m[0] | m[1] | m[2] | m[3]) != 0u)) {
+            const bool h0 = m[0] != 0u, h1 = m[1] != 0u, h2 = m[2] != 0u;
+            const uint32_t i = h0 ? 0u : (h1 ? 1u : (h2 ? 2u : 3u));
+            const uint32_t cur = h0 ? m[0] : (h1 ? m[1] : (h2 ? m[2] : m[3]));
+            const uint32_t pos = pos0 + 32u * (jl + i) + static_cast<uint32_t>(__ffs(cur) - 1);
+            const uint32_t rest = cur & (cur - 1u);
+            if (h0) m[0] = rest;
+            else if (h1) m[1] = rest;
+            else if (h2) m[2] = rest;
+            else m[3] = rest;
+            R.put(cur != 0u, pos, md);
         }
     }
+    R.drain();
 }
 
 }  // namespace dev
@@ -139,11 +158,11 @@ int noise_fill_grid(int sm_count) {
     return sm_count * n;
 }
 
-cudaError_t launch_noise_fill(int bits, const Seg *segs, int nseg, const uint32_t *fblk, uint32_t nblk, const Params &p,
+cudaError_t launch_noise_fill(int bits, const Seg *segs, int nseg, const uint32_t *fwin, uint32_t nunits, const Params &p,
                               int grid, cudaStream_t st) {
-    if (nblk == 0) return cudaSuccess;
-    if (bits == 8) dev::noise_fill_kernel<8><<<grid, dev::kFillThreads, 0, st>>>(segs, nseg, fblk, nblk, p);
-    else dev::noise_fill_kernel<12><<<grid, dev::kFillThreads, 0, st>>>(segs, nseg, fblk, nblk, p);
+    if (nunits == 0) return cudaSuccess;
+    if (bits == 8) dev::noise_fill_kernel<8><<<grid, dev::kFillThreads, 0, st>>>(segs, nseg, fwin, nunits, p);
+    else dev::noise_fill_kernel<12><<<grid, dev::kFillThreads, 0, st>>>(segs, nseg, fwin, nunits, p);
     return cudaGetLastError();
 }
 

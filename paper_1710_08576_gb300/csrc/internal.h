@@ -153,11 +153,11 @@ cudaError_t launch_mom(int bits, const MomChunk *chunks, int nchunks, const int3
                        cudaStream_t st);
 
 // Digital noise as a second pass over segments whose excision pass wrote 0 at the flagged
-// samples, the flag mask and every window's M and D (segments of fewer than 2^31 samples).
-// Segment s covers blocks [fblk[s], fblk[s + 1]) of kFillBlockWords mask words; nblk = fblk[nseg].
-constexpr int kFillBlockWords = 64;
+// samples, the flag mask, every window's count and every window's M and D (segments of fewer
+// than 2^31 samples). The pass's units are 128 mask words of a window (ceil(ceil(W / 32) / 128)
+// a window); segment s holds units [fwin[s], fwin[s + 1]), nunits = fwin[nseg].
 int noise_fill_grid(int sm_count);
-cudaError_t launch_noise_fill(int bits, const Seg *segs, int nseg, const uint32_t *fblk, uint32_t nblk, const Params &p,
+cudaError_t launch_noise_fill(int bits, const Seg *segs, int nseg, const uint32_t *fwin, uint32_t nunits, const Params &p,
                               int grid, cudaStream_t st);
 
 // Write n (<= kSegBatch) segment descriptors to dst (device) from kernel parameters.

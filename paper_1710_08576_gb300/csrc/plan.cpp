@@ -134,14 +134,14 @@ rfi_status plan_alloc_workspace(rfi_plan_s *P) {
     const size_t mc_b = mom ? al(sizeof(MomChunk) * P->mchunks.size()) : 0;
     const size_t pw_b = P->power ? al(2 * sizeof(uint64_t) * P->total_windows) : 0;
     const size_t var_b = al(sizeof(Variant) * P->variants.size());
-    std::vector<uint32_t> fblk;
+    std::vector<uint32_t> fwin;  // the fill pass: unit offsets of the segments (128 mask words a unit)
     if (P->fill) {
-        fblk.push_back(0);
+        fwin.push_back(0);
         for (int i = 0; i < P->S; ++i) {
-            const int64_t words = P->nwin[i] * ((P->W[i] + 31) / 32);
-            fblk.push_back(fblk.back() + static_cast<uint32_t>((words + kFillBlockWords - 1) / kFillBlockWords));
+            const int64_t upw = ((P->W[i] + 31) / 32 + 127) / 128;
+            fwin.push_back(fwin.back() + static_cast<uint32_t>(P->nwin[i] * upw));
         }
-        P->nfblk = fblk.back();
+        P->nfwin = fwin.back();
         P->fill_grid = noise_fill_grid(P->sm_count);
     }
     // one allocation, each array at the next 256-byte boundary
@@ -156,7 +156,7 @@ rfi_status plan_alloc_workspace(rfi_plan_s *P) {
     const size_t o_mom = mom ? take(md_b) : 0, o_mc = mom ? take(mc_b) : 0;
     const size_t o_pw = P->power ? take(pw_b) : 0;
     const size_t o_var = take(var_b);
-    const size_t o_fb = P->fill ? take(sizeof(uint32_t) * fblk.size()) : 0;
+    const size_t o_fw = P->fill ? take(sizeof(uint32_t) * fwin.size()) : 0;
     P->ws_bytes = off;
     if (P->ws) cudaFree(P->ws);
     P->ws = nullptr;
@@ -187,8 +187,8 @@ rfi_status plan_alloc_workspace(rfi_plan_s *P) {
                             cudaMemcpyHostToDevice));
     }
     if (P->fill) {
-        P->d_fblk = reinterpret_cast<uint32_t *>(b + o_fb);
-        RFI_CUDA(cudaMemcpy(P->d_fblk, fblk.data(), sizeof(uint32_t) * fblk.size(), cudaMemcpyHostToDevice));
+        P->d_fwin = reinterpret_cast<uint32_t *>(b + o_fw);
+        RFI_CUDA(cudaMemcpy(P->d_fwin, fwin.data(), sizeof(uint32_t) * fwin.size(), cudaMemcpyHostToDevice));
     }
     P->segs_valid = false;
     return RFI_OK;
@@ -218,7 +218,7 @@ rfi_status plan_enqueue_batched(rfi_plan_s *P, cudaStream_t st) {
         const Params p = plan_params(P);
         RFI_CUDA(launch_persistent(P->bits, plan_kernel_mode(P), P->shape, P->grid, P->d_segs, P->d_tiles,
                                    P->ntiles, p, &P->d_ctr->tile_counter, inject, st));
-        if (P->fill) RFI_CUDA(launch_noise_fill(P->bits, P->d_segs, P->S, P->d_fblk, P->nfblk, p, P->fill_grid, st));
+        if (P->fill) RFI_CUDA(launch_noise_fill(P->bits, P->d_segs, P->S, P->d_fwin, P->nfwin, p, P->fill_grid, st));
         return RFI_OK;
     }
     // Median of MAD (Eq. 3): M and D of every window, the sliding median of the MADs, then Eq. 1
@@ -233,7 +233,7 @@ rfi_status plan_enqueue_batched(rfi_plan_s *P, cudaStream_t st) {
                                P->d_tiles, P->ntiles, p, &P->d_ctr->tile_counter, 0, st));
     // the apply segments hold each window's M and its MoM: the noise spread of Eq. 3
     if (P->fill)
-        RFI_CUDA(launch_noise_fill(P->bits, P->d_segs + P->S, P->S, P->d_fblk, P->nfblk, p, P->fill_grid, st));
+        RFI_CUDA(launch_noise_fill(P->bits, P->d_segs + P->S, P->S, P->d_fwin, P->nfwin, p, P->fill_grid, st));
     return RFI_OK;
 }
 

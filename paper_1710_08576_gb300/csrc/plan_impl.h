@@ -62,10 +62,10 @@ struct rfi_plan_s {
     uint64_t *d_pow = nullptr;
     int out_format = RFI_OUT_SAME;  // fused output format
     // digital noise as a second pass (noise_fill): the excision pass replaces with 0, then the
-    // fill kernel writes the noise of every flagged sample; d_fblk: S + 1 block offsets
+    // fill kernel writes the noise of every flagged sample; d_fwin: S + 1 unit offsets
     bool fill = false;
-    uint32_t *d_fblk = nullptr;
-    uint32_t nfblk = 0;
+    uint32_t *d_fwin = nullptr;
+    uint32_t nfwin = 0;
     int fill_grid = 0;
     uint32_t *d_fmask = nullptr;  // flag masks of streams called without one (allocated on demand)
     std::vector<int64_t> fmask_off;
