@@ -133,6 +133,13 @@ typedef struct rfi_launch_shape {
     int32_t hist_copies;     /* 12-bit histogram copies (1, 2, 4); ignored for 8-bit */
     int32_t groups;          /* consumer groups per CTA, 1 or 2 (each with its own copy warp;
                                 2 needs consumer_warps <= 8) */
+    int32_t warp_split;      /* 1: every consumer warp runs every phase of a window; 2: four
+                                warps histogram, reduce and search each window while the other
+                                four replace the window before it (int8 zero, constant and
+                                threshold plans with 8 consumer warps in one group, neither
+                                power-metered, nor digital copies, nor another output format, nor
+                                write-flagged; RFI_ERR_UNSUPPORTED otherwise). 0 = choose: the
+                                autotuner tries both where the split form runs, otherwise 1 */
 } rfi_launch_shape;
 
 typedef struct rfi_plan_desc {

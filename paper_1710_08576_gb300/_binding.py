@@ -44,7 +44,7 @@ class RfiLaunchShape(ctypes.Structure):
     _fields_ = [("consumer_warps", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("stage_bytes", ctypes.c_int32),
                 ("dynamic_tiles", ctypes.c_int32), ("hist_copies", ctypes.c_int32),
-                ("groups", ctypes.c_int32)]
+                ("groups", ctypes.c_int32), ("warp_split", ctypes.c_int32)]
 
 
 class RfiPlanDesc(ctypes.Structure):

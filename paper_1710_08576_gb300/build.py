@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librfi.so")
 
-SOURCES = ["kernels8.cu", "kernels8m.cu", "kernels8f.cu", "kernels12.cu", "kernels.cu", "autotune.cu", "plan.cpp", "host_pipe.cpp",
+SOURCES = ["kernels8.cu", "kernels8m.cu", "kernels8f.cu", "kernels8s.cu", "kernels12.cu", "kernels.cu", "autotune.cu", "plan.cpp", "host_pipe.cpp",
            "noalloc.cu", "serve.cpp", "passes8.cu", "passes12.cu", "fill.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",

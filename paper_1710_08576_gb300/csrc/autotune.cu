@@ -101,6 +101,7 @@ bool cache_file_lookup(const std::string &key, Shape *out) {
         Shape s{};
         if (is >> s.consumer_warps >> s.stages >> s.ctas_per_sm >> s.stage_bytes >> s.dynamic_tiles >> s.hist_copies >>
             s.groups) {
+            if (!(is >> s.warp_split)) s.warp_split = 1;  // entries written before the split-warp form
             *out = s;
             found = true;  // the last entry for a key wins
         }
@@ -113,7 +114,7 @@ void cache_file_store(const std::string &key, const Shape &s) {
     if (!path || !*path) return;
     std::ofstream f(path, std::ios::app);
     f << key << '\t' << s.consumer_warps << ' ' << s.stages << ' ' << s.ctas_per_sm << ' ' << s.stage_bytes << ' '
-      << s.dynamic_tiles << ' ' << s.hist_copies << ' ' << s.groups << '\n';
+      << s.dynamic_tiles << ' ' << s.hist_copies << ' ' << s.groups << ' ' << s.warp_split << '\n';
 }
 
 struct Scratch {
@@ -216,11 +217,14 @@ rfi_status plan_autotune(rfi_plan_s *P, const rfi_launch_shape *req) {
             for (int stages : {1, 2, 3, 4, 6})
                 for (int mult : {1, 2, 4})
                     for (int dyn : {1, 2})
-                        for (int hc : {1, 2, 4}) {
+                        for (int hc : {1, 2, 4})
+                        for (int ws : {1, 2}) {
                             if (P->bits == 8 && hc != 1) continue;
                             if (!uniform && dyn == 2) continue;
                             if (grp == 2 && cw == 16) continue;
-                            Shape s{cw, stages, ctas, min_stage * mult, dyn, P->bits == 8 ? 1 : hc, grp};
+                            Shape s{cw, stages, ctas, min_stage * mult, dyn, P->bits == 8 ? 1 : hc, grp, ws};
+                            if (ws == 2 && !plan_warp_split_runs(P, s)) continue;
+                            if (req && req->warp_split && req->warp_split != ws) continue;
                             if (req) {
                                 if (req->consumer_warps && req->consumer_warps != cw) continue;
                                 if (req->stages && req->stages != stages) continue;

@@ -20,6 +20,9 @@ int persistent_occupancy_multi_b8(int, const Shape &);
 cudaError_t launch_persistent_fo_b8(int, const Shape &, int, const Seg *, const Tile *, int, const Params &,
                                     unsigned *, int, cudaStream_t);
 int persistent_occupancy_fo_b8(int, const Shape &);
+cudaError_t launch_persistent_split_b8(int, const Shape &, int, const Seg *, const Tile *, int, const Params &,
+                                       unsigned *, int, cudaStream_t);
+int persistent_occupancy_split_b8(int, const Shape &);
 int persistent_occupancy_mom_b12(int, const Shape &);
 cudaError_t launch_mom_b8(const MomChunk *, int, const int32_t *, int32_t *, int, cudaStream_t);
 cudaError_t launch_mom_b12(const MomChunk *, int, const int32_t *, int32_t *, int, cudaStream_t);
@@ -27,6 +30,7 @@ cudaError_t launch_stream_b8(int, int, const Seg &, int64_t, int64_t, const Para
 cudaError_t launch_stream_b12(int, int, const Seg &, int64_t, int64_t, const Params &, cudaStream_t);
 
 size_t persistent_smem_bytes(int bits, int mode, const Shape &s) {
+    mode = shape_mode(bits, mode, s);
     return bits == 8
                ? dev::layout<8>(s.hist_copies, s.stages, s.stage_bytes, s.consumer_warps, s.groups, mode).total
                : dev::layout<12>(s.hist_copies, s.stages, s.stage_bytes, s.consumer_warps, s.groups, mode).total;
@@ -39,6 +43,8 @@ size_t stream_smem_bytes(int bits, int mode, int consumer_warps, int ncopies, in
 }
 
 int persistent_occupancy(int bits, int mode, const Shape &s) {
+    mode = shape_mode(bits, mode, s);
+    if (mode & kModeWarpSplit) return persistent_occupancy_split_b8(mode, s);
     if (mode & kModeMulti) return bits == 8 ? persistent_occupancy_multi_b8(mode, s) : 0;
     if (mode & kModeFlaggedOnly) return bits == 8 ? persistent_occupancy_fo_b8(mode, s) : 0;
     if (mode >= kModeStats)
@@ -48,6 +54,9 @@ int persistent_occupancy(int bits, int mode, const Shape &s) {
 
 cudaError_t launch_persistent(int bits, int mode, const Shape &s, int grid, const Seg *segs, const Tile *tiles,
                               int ntiles, const Params &p, unsigned *counter, int inject, cudaStream_t st) {
+    mode = shape_mode(bits, mode, s);
+    if (mode & kModeWarpSplit)
+        return launch_persistent_split_b8(mode, s, grid, segs, tiles, ntiles, p, counter, inject, st);
     if (mode & kModeMulti)
         return bits == 8 ? launch_persistent_multi_b8(mode, s, grid, segs, tiles, ntiles, p, counter, inject, st)
                          : cudaErrorInvalidValue;

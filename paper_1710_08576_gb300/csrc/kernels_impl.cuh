@@ -24,6 +24,21 @@ struct StageMeta {
     int32_t pad[3];
 };
 
+// Split-warp form: a window handed from the histogram warps to the replace warps. Slot j is
+// filled by histogram warp 0 (lane 0) after waiting for its empty mbarrier, announced through its
+// full mbarrier, and released by the last replace warp to finish the window.
+constexpr int kSplitSlots = 4;
+struct __align__(16) SplitSlot {
+    RepShared rep;    // the window's M, D, threshold and replacement values
+    int64_t widx;     // window of the segment
+    int32_t stage;    // stage buffer holding it
+    int32_t k;        // window of the stage's tile
+    int32_t last;     // the tile's last window: its replace releases the stage
+    int32_t end;      // no more windows
+    int32_t upar;     // parity of the stage's fill
+    int32_t pad;
+};
+
 // Dynamic shared memory: the histogram at offset 0 (8-bit: one table for all groups; 12-bit:
 // per group; none for the apply passes of Eq. 3), then one block per consumer group
 // (cumulative counts, control block, mbarriers, stage descriptors), then the stage buffers of
@@ -38,6 +53,7 @@ struct Layout {
     int atile;                // apply passes: thresholds and counts of the current tile (0: none)
     int cps;                  // digital copy: per-variant state inside a group block (0: none)
     int mt;                   // 8-bit plain excision and estimation: multi-window tile state (0: none)
+    int split;                // split-warp form: the hand-over slots (0: none)
     int stage;      // first stage buffer; group g stage s at stage + (g * stages + s) * stage_bytes
     int total;
 };
@@ -51,8 +67,11 @@ __host__ __device__ inline Layout layout(int ncopies, int stages, int stage_byte
     L.cum = 0;
     // (multi-window tiles: up to kMultiMax slots of 16-bit counts)
     L.ctl = align_up(multi ? Geo<BITS>::kCumWords * 2 * kMultiMax : Geo<BITS>::kCumWords * 4, 128);
+    const bool split = (mode & kModeWarpSplit) != 0;
     L.bar = align_up(L.ctl + static_cast<int>(sizeof(Ctl)), 128);
-    L.meta = align_up(L.bar + (2 * kMaxStages + 1) * 8, 128);
+    // full and empty barriers per stage, the test hook's barrier, and for the split-warp form a
+    // full and an empty barrier per hand-over slot
+    L.meta = align_up(L.bar + (2 * kMaxStages + 1 + (split ? 2 * kSplitSlots : 0)) * 8, 128);
     const int meta_end = align_up(L.meta + kMaxStages * static_cast<int>(sizeof(StageMeta)), 128);
     const bool noise = ((mode & 3) == 3 || (mode & kModeCopies) != 0) && (mode & kModeStats) == 0;
     L.nlist = noise ? meta_end : 0;
@@ -75,6 +94,8 @@ __host__ __device__ inline Layout layout(int ncopies, int stages, int stage_byte
     const int cps_end = copies ? align_up(amd_end + static_cast<int>(sizeof(CopyShared)), 128) : amd_end;
     L.mt = multi ? cps_end : 0;
     L.grp_size = multi ? align_up(cps_end + static_cast<int>(sizeof(MultiTile)), 128) : cps_end;
+    L.split = split ? L.grp_size : 0;
+    if (split) L.grp_size = align_up(L.grp_size + kSplitSlots * static_cast<int>(sizeof(SplitSlot)), 128);
     L.stage = L.grp + groups * L.grp_size;
     L.total = L.stage + groups * stages * stage_bytes;
     return L;
@@ -132,6 +153,153 @@ __device__ __forceinline__ Win make_win(const Seg &sg, int64_t w, const uint8_t 
 // shared memory never grants.
 constexpr int min_ctas_per_sm(int cw, int g) { return g != 1 ? 0 : (cw == 8 ? 3 : (cw == 4 ? 4 : 0)); }
 
+// ------------------------------------------------------------------ split-warp consumers
+// The consumer warps of the split-warp form (int8, zero / constant / threshold, one group of 8
+// consumer warps). Warps 0-3 (the histogram warps, named barrier 1) take the stages in order:
+// per window the histogram, the reduce and, on warp 0, the scan and the searches, whose result
+// warp 0 hands over in a slot; they go on to the next window's histogram at once, so warp 0's
+// searches overlap the other histogram warps' work. Warps 4-7 (the replace warps, named barrier 2)
+// take the slots in order and run the replace pass of each window (Eq. 1 and Eq. 2) from the
+// stage, which the last of them to finish releases after the tile's last window; they write the
+// counts, warp 0 of the histogram warps M and D. The histogram table keeps its running sums as in
+// the joint form. Every wait is bounded; the first barrier after each wait agrees on a timeout
+// among its warps, and a timeout or the end of the work list reaches the replace warps through
+// a slot marked end (or, if the hand-over itself timed out, through their own bounded waits).
+template <int MODE, int CW>
+__device__ bool split_consumers(const Shm &sm, uint8_t *gb, const Layout &L, StageMeta *meta, uint8_t *stage0,
+                                int stages, int stage_bytes, uint32_t bar0, const Params &p, int tid) {
+    static_assert(CW == 8, "four histogram and four replace warps");
+    constexpr int NH = 4, NR = CW - NH, TH = NH * 32, TR = NR * 32;
+    constexpr int RMODE = MODE & 3;
+    const int lane = tid & 31;
+    SplitSlot *slots = reinterpret_cast<SplitSlot *>(gb + L.split);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (kMaxStages + s); };
+    auto slot_full = [&](int j) { return bar0 + 8u * (2 * kMaxStages + 1 + j); };
+    auto slot_empty = [&](int j) { return bar0 + 8u * (2 * kMaxStages + 1 + kSplitSlots + j); };
+    bool tmo = false;
+    if (tid < TH) {
+        RowSums rs = {{0u, 0u}};
+        int seq = 0;          // windows handed over so far
+        bool stop = false;    // warp 0: a hand-over timed out
+        for (int it = 0;; ++it) {
+            const int s = it % stages;
+            const int u = it / stages;
+            const bool ok = mbar_wait_bounded(full_bar(s), u & 1, kWaitTimeoutNs);
+            if (named_bar_or(1, TH, !ok || stop)) {
+                tmo = true;
+                break;
+            }
+            if (meta[s].tidx < 0) break;  // the end of the work list, seen alike by every thread
+            const Tile tl = meta[s].tile;
+            const Seg &sg = meta[s].seg;
+            uint8_t *stage = stage0 + s * stage_bytes;
+            if (!sg.vec) {
+                const uint8_t *src = sg.in + static_cast<int64_t>(tl.w0) * sg.W;
+                for (int i = tid; i < static_cast<int>(tl.bytes); i += TH) stage[i] = src[i];
+                named_bar(1, TH);
+            }
+            bool brk = false;
+            for (uint32_t k = 0; k < tl.nw; ++k) {
+                const int64_t widx = static_cast<int64_t>(tl.w0) + k;
+                const Win win = make_win(sg, widx, stage + k * sg.W, 1);
+                phase_histogram<8, TH, 128>(sm, win, tid, 0);
+                // warp 0 has finished the previous window's searches and hand-over
+                if (named_bar_or(1, TH, stop)) {
+                    brk = true;
+                    break;
+                }
+                phase_reduce8_counts<TH, 128>(sm, tid, rs);
+                named_bar(1, TH);
+                if (tid < 32) {
+                    phase_scan8_warp(sm, win.n, lane);
+                    const int j = seq % kSplitSlots, use = seq / kSplitSlots;
+                    int okj = 1;
+                    if (use > 0 && lane == 0) okj = mbar_wait_bounded(slot_empty(j), (use - 1) & 1, kWaitTimeoutNs);
+                    okj = __shfl_sync(0xFFFFFFFFu, okj, 0);
+                    phase_search<8>(sm, win.n, lane, p.kq, p.cval);
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (okj) {
+                            SplitSlot &sl = slots[j];
+                            sl.rep = sm.ctl->rep;
+                            sl.widx = widx;
+                            sl.stage = s;
+                            sl.k = static_cast<int32_t>(k);
+                            sl.last = k + 1 == tl.nw ? 1 : 0;
+                            sl.end = 0;
+                            sl.upar = u & 1;
+                            if (sg.med) sg.med[widx] = sm.ctl->rep.M;
+                            if (sg.mad) sg.mad[widx] = sm.ctl->rep.D;
+                            mbar_arrive(slot_full(j));
+                        }
+                    }
+                    if (!okj) stop = true;
+                }
+                ++seq;
+            }
+            if (brk) {
+                tmo = true;
+                break;
+            }
+        }
+        if (tid < 32 && !tmo) {  // the end mark for the replace warps
+            const int j = seq % kSplitSlots, use = seq / kSplitSlots;
+            int okj = 1;
+            if (use > 0 && lane == 0) okj = mbar_wait_bounded(slot_empty(j), (use - 1) & 1, kWaitTimeoutNs);
+            if (lane == 0 && okj) {
+                slots[j].end = 1;
+                mbar_arrive(slot_full(j));
+            }
+            if (!__shfl_sync(0xFFFFFFFFu, okj, 0)) tmo = true;
+        }
+    } else {
+        const int rtid = tid - TH;
+        Shm sr = sm;
+        sr.bar_id = 2;
+        int seq = 0, par = 0;
+        const KeysPre key{p};
+        for (;;) {
+            const int j = seq % kSplitSlots, use = seq / kSplitSlots;
+            const bool ok = mbar_wait_bounded(slot_full(j), use & 1, kWaitTimeoutNs);
+            if (named_bar_or(2, TR, !ok)) {
+                tmo = true;
+                break;
+            }
+            const SplitSlot &sl = slots[j];
+            if (sl.end) break;
+            const int s = sl.stage;
+            // the stage's fill has completed; waiting on it orders its bytes for these threads
+            mbar_wait_bounded(full_bar(s), static_cast<uint32_t>(sl.upar), kWaitTimeoutNs);
+            const Seg &sg = meta[s].seg;
+            const int64_t widx = sl.widx;
+            const Win win = make_win(sg, widx, stage0 + s * stage_bytes + sl.k * sg.W, 1);
+            const Rep r = load_rep(sl.rep);
+            Pow pw = {0u, 0u};
+            uint32_t f = phase_replace<8, RMODE, TR, false, KeysPre, 0, false>(sr, win, r, key, rtid,
+                                                                              &sm.ctl->ncount[par], pw, &sl.rep);
+            f = __reduce_add_sync(0xFFFFFFFFu, f);
+            if (lane == 0) {
+                if (f) atomicAdd(&sm.ctl->count[par], f);
+                __threadfence_block();
+                if (atomicAdd(&sm.ctl->done[par], 1u) == NR - 1) {
+                    // the last replace warp of the window: every count is in, every read done
+                    __threadfence_block();
+                    const uint32_t cnt = atomicExch(&sm.ctl->count[par], 0u);
+                    sm.ctl->done[par] = 0u;
+                    if (sg.counts) sg.counts[widx] = cnt;
+                    sm.ctl->flagged += cnt;
+                    if (sl.last) mbar_arrive(empty_bar(s));
+                    mbar_arrive(slot_empty(j));
+                }
+            }
+            ++seq;
+            par ^= 1;
+        }
+    }
+    return !tmo;
+}
+
 template <int BITS, int MODE, int CW, int G>
 __global__ void __launch_bounds__(G *(CW + 1) * 32, min_ctas_per_sm(CW, G))
 persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, int ntiles, Params p,
@@ -165,6 +333,8 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
             mbar_init(empty_bar(s), 1);
         }
         mbar_init(inj_bar, 1);
+        if (MODE & kModeWarpSplit)
+            for (int j = 0; j < 2 * kSplitSlots; ++j) mbar_init(inj_bar + 8u * (1 + j), 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -285,6 +455,15 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
     // ---------------- consumer warps of group g
     if (inject_timeout && blockIdx.x == 0 && g == 0 && tid == 0) {
         if (!mbar_wait_bounded(inj_bar, 0, kInjectTimeoutNs)) atomicOr(p.status, kStatusTimeout);
+    }
+    if constexpr (BITS == 8 && G == 1 && (MODE & kModeWarpSplit) != 0) {
+        if (!split_consumers<MODE & 3, CW>(sm, gb, L, meta, stage0, stages, stage_bytes, bar0, p, tid)) {
+            atomicOr(p.status, kStatusTimeout);
+            atomicExch(&sm.ctl->abort, 1u);
+        }
+        named_bar(3, T);  // every consumer thread of the CTA
+        if (tid == 0 && sm.ctl->flagged) atomicAdd(p.flagged, sm.ctl->flagged);
+        return;
     }
     int par = 0;  // window parity
     bool timed_out = false;

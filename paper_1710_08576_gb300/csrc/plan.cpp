@@ -31,7 +31,8 @@ bool valid_shape(const rfi_launch_shape &s) {
            s.ctas_per_sm <= 4 && s.stage_bytes >= 0 && s.stage_bytes <= 227 * 1024 && s.dynamic_tiles >= 0 &&
            s.dynamic_tiles <= 2 && s.hist_copies >= 0 && s.hist_copies <= 4 && s.hist_copies != 3 &&
            (s.consumer_warps == 0 || s.consumer_warps == 4 || s.consumer_warps == 8 || s.consumer_warps == 16) &&
-           s.groups >= 0 && s.groups <= 2 && !(s.groups == 2 && s.consumer_warps == 16);
+           s.groups >= 0 && s.groups <= 2 && !(s.groups == 2 && s.consumer_warps == 16) && s.warp_split >= 0 &&
+           s.warp_split <= 2;
 }
 
 }  // namespace
@@ -83,8 +84,16 @@ rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req) {
         if (occ_apply < 1) return cudaGetLastError() != cudaSuccess ? RFI_ERR_CUDA : RFI_ERR_UNSUPPORTED;
         P->grid_apply = P->sm_count * occ_apply;  // clamped to the tile count with the grid
     }
+    // the split-warp form only where it runs: int8 zero / constant / threshold, one group of 8
+    s.warp_split = (req && req->warp_split) ? req->warp_split : 1;
+    if (s.warp_split == 2 && !plan_warp_split_runs(P, s)) return RFI_ERR_UNSUPPORTED;
     P->shape = s;
     return RFI_OK;
+}
+
+bool plan_warp_split_runs(const rfi_plan_s *P, const Shape &s) {
+    return P->kmom < 2 && !P->power && P->ncopy == 0 && P->out_format == RFI_OUT_SAME &&
+           warp_split_runs(P->bits, plan_kernel_mode(P), s);
 }
 
 rfi_status plan_build_tiles(rfi_plan_s *P) {
@@ -773,6 +782,7 @@ rfi_status rfi_plan_get_info(rfi_plan_t P, rfi_plan_info *info) {
     info->shape.dynamic_tiles = P->shape.dynamic_tiles;
     info->shape.hist_copies = P->shape.hist_copies;
     info->shape.groups = P->shape.groups;
+    info->shape.warp_split = P->shape.warp_split;
     info->sm_count = P->sm_count;
     info->kernels_per_call = (P->flags & RFI_PLAN_PER_STREAM) ? P->S : (P->kmom >= 2 ? 3 : 1) + (P->fill ? 1 : 0);
     return RFI_OK;

@@ -94,6 +94,8 @@ struct rfi_plan_s {
 namespace rfi {
 
 rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req);
+// Whether the split-warp form (kModeWarpSplit) can run this plan with shape s.
+bool plan_warp_split_runs(const rfi_plan_s *P, const Shape &s);
 rfi_status plan_build_tiles(rfi_plan_s *P);
 rfi_status plan_alloc_workspace(rfi_plan_s *P);
 rfi_status plan_enqueue_batched(rfi_plan_s *P, cudaStream_t st);

@@ -92,6 +92,7 @@ def test_constants_match_header(tmp_path):
     dict(mode=4), dict(mode=-1), dict(flags=0x80000000),
     dict(flags=rfi.RFI_PLAN_PER_STREAM | rfi.RFI_PLAN_GRAPH),
     dict(shape=dict(consumer_warps=5)), dict(shape=dict(stages=9)), dict(shape=dict(hist_copies=3)),
+    dict(shape=dict(warp_split=3)), dict(shape=dict(warp_split=-1)),
 ])
 def test_invalid_plan_arguments_fail_before_cuda(kw):
     args = dict(bits=8, stream_len=[4096], window_len=[1024], k=3.0, mode=0)
