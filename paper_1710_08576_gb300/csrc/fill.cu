@@ -26,7 +26,7 @@ namespace dev {
 
 constexpr int kFillThreads = 256;
 constexpr int kFillRing = 64;   // positions a warp's ring holds: fewer than 32 wait between steps
-constexpr int kFillDense = 8;   // flags from which a mask word is expanded whole
+constexpr int kFillDense = 2;   // flags from which a mask word is expanded whole
 
 template <int BITS>
 __device__ __forceinline__ void fill_store(uint8_t *out, uint32_t pos, int32_t z) {
