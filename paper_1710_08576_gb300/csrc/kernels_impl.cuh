@@ -511,8 +511,9 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
             }
         }
         if constexpr (BITS == 8 && G == 1 && (MODE & kModeMulti) != 0) {
-            // several small full windows of 2^lw samples: eight (W <= 2048) or four at a time share
-            // the histogram table, the reduce, the barriers and the searches
+            // several small full windows of 2^lw samples: eight (W <= 2048, or a tile of eight or
+            // more) or four at a time share the histogram table, the reduce, the barriers and the
+            // searches
             const uint32_t W = static_cast<uint32_t>(sg.W);
             if (sg.vec && tl.nw >= 2u && W >= 512u && W <= 8192u && (W & (W - 1u)) == 0u && tl.bytes == tl.nw * W) {
                 if (dirty) {
@@ -521,7 +522,7 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
                     dirty = false;
                 }
                 const int lw = 31 - __clz(static_cast<int>(W));
-                const uint32_t K = W <= 2048u ? 8u : 4u;
+                const uint32_t K = (W <= 2048u || tl.nw >= 8u) ? 8u : 4u;
                 for (uint32_t k0 = 0; k0 < tl.nw && alive; k0 += K) {
                     const int nwk = static_cast<int>(tl.nw - k0 < K ? tl.nw - k0 : K);
                     const uint32_t rel = k0 + K >= tl.nw ? empty_bar(s) : 0u;

@@ -62,9 +62,14 @@ rfi_status plan_choose_shape(rfi_plan_s *P, const rfi_launch_shape *req) {
         if ((req && req->groups > 1) || s.consumer_warps > 8) return RFI_ERR_UNSUPPORTED;
         s.groups = 1;
     }
-    s.stage_bytes = std::max(min_stage, (req && req->stage_bytes) ? req->stage_bytes : 16384);
+    // a Median-of-MAD plan on 4096-sample windows takes one 32 KiB stage: tiles of eight windows
+    // share one histogram table in the multi-window estimation pass
+    bool mom4096 = P->kmom >= 2 && P->bits == 8;
+    for (int i = 0; i < P->S && mom4096; ++i) mom4096 = P->W[i] == 4096 && P->len[i] >= 8 * 4096;
+    const bool mom_stage = mom4096 && !(req && (req->stage_bytes || req->stages));
+    s.stage_bytes = std::max(min_stage, (req && req->stage_bytes) ? req->stage_bytes : (mom_stage ? 32768 : 16384));
     s.stage_bytes = (s.stage_bytes + 127) / 128 * 128;
-    s.stages = (req && req->stages) ? req->stages : 2;
+    s.stages = (req && req->stages) ? req->stages : (mom_stage ? 1 : 2);
     s.hist_copies = P->bits == 8 ? 1 : ((req && req->hist_copies) ? req->hist_copies : 2);
     s.dynamic_tiles = (req && req->dynamic_tiles) ? req->dynamic_tiles : (uniform ? 2 : 1);
     const int want_ctas = (req && req->ctas_per_sm) ? req->ctas_per_sm : 4;  // as many as fit, up to 4

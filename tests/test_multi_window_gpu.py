@@ -2,7 +2,8 @@
 
 Plans with windows of 2^l = 512..8192 samples run the instantiation that histograms several
 windows of a tile at once in the lane-striped table: eight for windows of at most 2048 samples
-(window slot g in lanes 4g..4g+3), four for 4096 and 8192 (lanes 8g..8g+7). It reduces them in
+and for tiles of eight or more larger windows (window slot g in lanes 4g..4g+3), otherwise four
+(lanes 8g..8g+7). It reduces them in
 one pass that also clears the table and searches them on several warps in parallel. These cases
 pin down what that adds to the per-window path: tiles of every remainder of the slot count
 (sub-tiles of 1 to 7 windows), the switch between multi-window tiles and per-window tiles
@@ -62,6 +63,22 @@ def test_multi_and_per_window_tiles_in_one_kernel(cuda, rfi, form, dynamic):
         got, st, totals, _ = gpu_run(rfi, xs, wins, 8, 3.0, mode, 0, 9, flags=form | 0x20, shape=shape)
         assert st == 0
         assert_same(got, ref, "mode %d form %#x dynamic %d" % (mode, form, dynamic))
+
+
+@pytest.mark.parametrize("W,sb", [(4096, 32768), (8192, 65536), (4096, 65536)])
+@pytest.mark.parametrize("mode", [0, 2, 3])
+def test_eight_slots_for_large_windows(cuda, rfi, W, sb, mode):
+    """Stages of eight or more 4096- or 8192-sample windows take eight window slots (four lanes
+    each) per tile instead of four; tiles of fewer (a stream's last) take four."""
+    per = sb // W
+    lens = [n * W for n in (1, 3, 7, 8, 9, per, per + 3, 2 * per + 5)] + [5 * W + 99]
+    xs = _streams(lens, 700 + W + sb + mode)
+    shape = dict(consumer_warps=8, stages=1, ctas_per_sm=1, dynamic_tiles=1, groups=1, stage_bytes=sb)
+    wins = [W] * len(xs)
+    ref = oracle_run(xs, wins, 8, 3.0, mode, 0, 7)
+    got, st, totals, _ = gpu_run(rfi, xs, wins, 8, 3.0, mode, 0, 7, shape=shape)
+    assert st == 0
+    assert_same(got, ref, "W %d stage %d mode %d" % (W, sb, mode))
 
 
 def test_multi_window_with_unaligned_buffers_falls_back(cuda, rfi):
