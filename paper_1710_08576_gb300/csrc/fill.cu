@@ -5,11 +5,11 @@
 // kernel then overwrites the flagged samples with M + the Philox noise of spread 1.4826·D, keyed
 // by the absolute sample index as always, so the result is the same bits as the one-pass form.
 //
-// Work: every 128 mask words of a window (4096 samples, fewer at a window's end) are a unit;
+// Work: every 256 mask words of a window (8192 samples, fewer at a window's end) are a unit;
 // warp g of the grid takes units g, g + nwarps, ... (segment s holds units [fwin[s], fwin[s + 1]),
-// its windows in order, ceil(mask words / 128) units each). A unit of a window whose count is 0
-// is skipped. Lane l reads the unit's words 4l .. 4l + 3, and the warp moves their flagged
-// samples into its ring of positions:
+// its windows in order, ceil(mask words / 256) units each). A unit of a window whose count is 0
+// is skipped. The unit goes in two halves of 128 words: lane l reads words 4l .. 4l + 3 of a
+// half, and the warp moves their flagged samples into its ring of positions:
 //  - a word with at least kFillDense flags goes whole: lane j tests bit j and a ballot with a
 //    prefix popcount gives each flagged lane its place in the ring;
 //  - from the other words every lane gives up one flag per step (its lowest remaining one),
@@ -94,54 +94,56 @@ __global__ void __launch_bounds__(kFillThreads) noise_fill_kernel(const Seg *__r
         }
         const Seg &g = segs[s];
         const uint32_t mw = static_cast<uint32_t>(g.mask_words);
-        const uint32_t upw = (mw + 127u) >> 7;  // units per window
+        const uint32_t upw = (mw + 255u) >> 8;  // units per window
         const uint32_t local = u - fwin[s];
         const uint32_t k = local / upw;
-        const uint32_t j0 = (local - k * upw) << 7;
+        const uint32_t j00 = (local - k * upw) << 8;
         if (g.counts && g.counts[k] == 0u) continue;
         const uint32_t md = (static_cast<uint32_t>(g.med[k]) & 0xFFFFu) | (static_cast<uint32_t>(g.mad[k]) << 16);
         const uint32_t pos0 = k * static_cast<uint32_t>(g.W);
         const uint32_t *mk = g.mask + static_cast<size_t>(k) * mw;
-        const uint32_t jl = j0 + 4u * static_cast<uint32_t>(lane);  // this lane's first word
-        uint32_t m[4];
-        if ((mw & 3u) == 0u && (reinterpret_cast<uintptr_t>(mk) & 15u) == 0u) {
-            const uint4 a = jl < mw ? *reinterpret_cast<const uint4 *>(mk + jl) : make_uint4(0u, 0u, 0u, 0u);
-            m[0] = a.x;
-            m[1] = a.y;
-            m[2] = a.z;
-            m[3] = a.w;
-        } else {
+        for (uint32_t j0 = j00; j0 < j00 + 256u && j0 < mw; j0 += 128u) {
+            const uint32_t jl = j0 + 4u * static_cast<uint32_t>(lane);  // this lane's first word
+            uint32_t m[4];
+            if ((mw & 3u) == 0u && (reinterpret_cast<uintptr_t>(mk) & 15u) == 0u) {
+                const uint4 a = jl < mw ? *reinterpret_cast<const uint4 *>(mk + jl) : make_uint4(0u, 0u, 0u, 0u);
+                m[0] = a.x;
+                m[1] = a.y;
+                m[2] = a.z;
+                m[3] = a.w;
+            } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) m[i] = jl + i < mw ? mk[jl + i] : 0u;
-        }
-        if (!__any_sync(0xFFFFFFFFu, (m[0] | m[1] | m[2] | m[3]) != 0u)) continue;
-        // dense words, one at a time over the whole warp
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t wi = m[i];
-            const bool d = __popc(wi) >= kFillDense;
-            uint32_t dense = __ballot_sync(0xFFFFFFFFu, d);
-            if (d) m[i] = 0u;
-            while (dense) {
-                const int src = __ffs(dense) - 1;
-                dense &= dense - 1u;
-                const uint32_t w = __shfl_sync(0xFFFFFFFFu, wi, src);
-                const uint32_t pos = pos0 + 32u * (j0 + 4u * static_cast<uint32_t>(src) + i) + static_cast<uint32_t>(lane);
-                R.put(((w >> lane) & 1u) != 0u, pos, md);
+                for (int i = 0; i < 4; ++i) m[i] = jl + i < mw ? mk[jl + i] : 0u;
             }
-        }
-        // the other words: each lane gives up its lowest remaining flag per step
-        while (__any_sync(0xFFFFFFFFu, (m[0] | m[1] | m[2] | m[3]) != 0u)) {
-            const bool h0 = m[0] != 0u, h1 = m[1] != 0u, h2 = m[2] != 0u;
-            const uint32_t i = h0 ? 0u : (h1 ? 1u : (h2 ? 2u : 3u));
-            const uint32_t cur = h0 ? m[0] : (h1 ? m[1] : (h2 ? m[2] : m[3]));
-            const uint32_t pos = pos0 + 32u * (jl + i) + static_cast<uint32_t>(__ffs(cur) - 1);
-            const uint32_t rest = cur & (cur - 1u);
-            if (h0) m[0] = rest;
-            else if (h1) m[1] = rest;
-            else if (h2) m[2] = rest;
-            else m[3] = rest;
-            R.put(cur != 0u, pos, md);
+            if (!__any_sync(0xFFFFFFFFu, (m[0] | m[1] | m[2] | m[3]) != 0u)) continue;  // on to the next half
+            // dense words, one at a time over the whole warp
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t wi = m[i];
+                const bool d = __popc(wi) >= kFillDense;
+                uint32_t dense = __ballot_sync(0xFFFFFFFFu, d);
+                if (d) m[i] = 0u;
+                while (dense) {
+                    const int src = __ffs(dense) - 1;
+                    dense &= dense - 1u;
+                    const uint32_t w = __shfl_sync(0xFFFFFFFFu, wi, src);
+                    const uint32_t pos = pos0 + 32u * (j0 + 4u * static_cast<uint32_t>(src) + i) + static_cast<uint32_t>(lane);
+                    R.put(((w >> lane) & 1u) != 0u, pos, md);
+                }
+            }
+            // the other words: each lane gives up its lowest remaining flag per step
+            while (__any_sync(0xFFFFFFFFu, (m[0] | m[1] | m[2] | m[3]) != 0u)) {
+                const bool h0 = m[0] != 0u, h1 = m[1] != 0u, h2 = m[2] != 0u;
+                const uint32_t i = h0 ? 0u : (h1 ? 1u : (h2 ? 2u : 3u));
+                const uint32_t cur = h0 ? m[0] : (h1 ? m[1] : (h2 ? m[2] : m[3]));
+                const uint32_t pos = pos0 + 32u * (jl + i) + static_cast<uint32_t>(__ffs(cur) - 1);
+                const uint32_t rest = cur & (cur - 1u);
+                if (h0) m[0] = rest;
+                else if (h1) m[1] = rest;
+                else if (h2) m[2] = rest;
+                else m[3] = rest;
+                R.put(cur != 0u, pos, md);
+            }
         }
     }
     R.drain();

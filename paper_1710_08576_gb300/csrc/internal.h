@@ -169,7 +169,7 @@ cudaError_t launch_mom(int bits, const MomChunk *chunks, int nchunks, const int3
 
 // Digital noise as a second pass over segments whose excision pass wrote 0 at the flagged
 // samples, the flag mask, every window's count and every window's M and D (segments of fewer
-// than 2^31 samples). The pass's units are 128 mask words of a window (ceil(ceil(W / 32) / 128)
+// than 2^31 samples). The pass's units are 256 mask words of a window (ceil(ceil(W / 32) / 256)
 // a window); segment s holds units [fwin[s], fwin[s + 1]), nunits = fwin[nseg].
 int noise_fill_grid(int sm_count);
 cudaError_t launch_noise_fill(int bits, const Seg *segs, int nseg, const uint32_t *fwin, uint32_t nunits, const Params &p,

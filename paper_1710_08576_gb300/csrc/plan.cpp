@@ -148,11 +148,11 @@ rfi_status plan_alloc_workspace(rfi_plan_s *P) {
     const size_t mc_b = mom ? al(sizeof(MomChunk) * P->mchunks.size()) : 0;
     const size_t pw_b = P->power ? al(2 * sizeof(uint64_t) * P->total_windows) : 0;
     const size_t var_b = al(sizeof(Variant) * P->variants.size());
-    std::vector<uint32_t> fwin;  // the fill pass: unit offsets of the segments (128 mask words a unit)
+    std::vector<uint32_t> fwin;  // the fill pass: unit offsets of the segments (256 mask words a unit)
     if (P->fill) {
         fwin.push_back(0);
         for (int i = 0; i < P->S; ++i) {
-            const int64_t upw = ((P->W[i] + 31) / 32 + 127) / 128;
+            const int64_t upw = ((P->W[i] + 31) / 32 + 255) / 256;
             fwin.push_back(fwin.back() + static_cast<uint32_t>(P->nwin[i] * upw));
         }
         P->nfwin = fwin.back();
