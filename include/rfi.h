@@ -136,9 +136,9 @@ typedef struct rfi_launch_shape {
     int32_t warp_split;      /* 1: every consumer warp runs every phase of a window; 2: four
                                 warps histogram, reduce and search each window while the other
                                 four replace the window before it (int8 zero, constant and
-                                threshold plans with 8 consumer warps in one group, neither
-                                power-metered, nor digital copies, nor another output format, nor
-                                write-flagged; RFI_ERR_UNSUPPORTED otherwise). 0 = choose: the
+                                threshold plans with 8 consumer warps in one group, also
+                                write-flagged, but neither power-metered, nor digital copies, nor
+                                another output format; RFI_ERR_UNSUPPORTED otherwise). 0 = choose: the
                                 autotuner tries both where the split form runs, otherwise 1 */
 } rfi_launch_shape;
 

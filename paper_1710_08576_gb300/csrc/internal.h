@@ -39,10 +39,10 @@ constexpr int kModeMulti = 256;
 // chunks without a flagged sample are not stored, and with digital noise no chunk is (the noise
 // pass writes every flagged sample). Its own instantiation, like kModeMulti.
 constexpr int kModeFlaggedOnly = 512;
-// Flag bit of the split-warp form (8-bit zero, constant and threshold modes, one group of 8
-// consumer warps): warps 0-3 histogram, reduce and search window n + 1 while warps 4-7 replace
-// window n, handing each window's thresholds over through a ring of slots with mbarriers. Its
-// own instantiation, chosen by the launch shape (Shape::warp_split == 2).
+// Flag bit of the split-warp form (8-bit zero, constant and threshold modes, also write-flagged,
+// one group of 8 consumer warps): warps 0-3 histogram, reduce and search window n + 1 while
+// warps 4-7 replace window n, handing each window's thresholds over through a ring of slots with
+// mbarriers. Its own instantiation, chosen by the launch shape (Shape::warp_split == 2).
 constexpr int kModeWarpSplit = 1024;
 
 // One variant of a digital-copy pass.
@@ -135,7 +135,8 @@ struct Shape {
 // The mode a persistent launch of this shape runs: mode | kModeWarpSplit when the shape asks for
 // the split-warp form and the mode and shape allow it.
 inline bool warp_split_runs(int bits, int mode, const Shape &s) {
-    return bits == 8 && mode >= 0 && mode <= 2 && s.consumer_warps == 8 && s.groups == 1;
+    const int base = mode & ~kModeFlaggedOnly;  // the write-flagged form splits too
+    return bits == 8 && base >= 0 && base <= 2 && s.consumer_warps == 8 && s.groups == 1;
 }
 inline int shape_mode(int bits, int mode, const Shape &s) {
     return s.warp_split == 2 && warp_split_runs(bits, mode, s) ? (mode | kModeWarpSplit) : mode;

@@ -1,10 +1,11 @@
 // 8-bit instantiations of the split-warp form of the persistent kernel (zero, constant and
-// threshold replacement; one consumer group of 8 warps: 4 histogram warps, 4 replace warps).
+// threshold replacement, also write-flagged; one consumer group of 8 warps: 4 histogram warps,
+// 4 replace warps).
 #include "kernels_impl.cuh"
 
 namespace rfi {
 
-static_assert(kModeWarpSplit == 1024, "mode numbers of the cases below");
+static_assert(kModeWarpSplit == 1024 && kModeFlaggedOnly == 512, "mode numbers of the cases below");
 
 #define RFI_DISPATCH_SPLIT(FN, MODE, CW, G, ...)                                                      \
     do {                                                                                              \
@@ -12,6 +13,9 @@ static_assert(kModeWarpSplit == 1024, "mode numbers of the cases below");
             RFI_CASE_MCG(8, FN, 1024, 8, 1, __VA_ARGS__)                                              \
             RFI_CASE_MCG(8, FN, 1025, 8, 1, __VA_ARGS__)                                              \
             RFI_CASE_MCG(8, FN, 1026, 8, 1, __VA_ARGS__)                                              \
+            RFI_CASE_MCG(8, FN, 1536, 8, 1, __VA_ARGS__)                                              \
+            RFI_CASE_MCG(8, FN, 1537, 8, 1, __VA_ARGS__)                                              \
+            RFI_CASE_MCG(8, FN, 1538, 8, 1, __VA_ARGS__)                                              \
             default: break;                                                                           \
         }                                                                                             \
     } while (0)

@@ -154,8 +154,8 @@ __device__ __forceinline__ Win make_win(const Seg &sg, int64_t w, const uint8_t 
 constexpr int min_ctas_per_sm(int cw, int g) { return g != 1 ? 0 : (cw == 8 ? 3 : (cw == 4 ? 4 : 0)); }
 
 // ------------------------------------------------------------------ split-warp consumers
-// The consumer warps of the split-warp form (int8, zero / constant / threshold, one group of 8
-// consumer warps). Warps 0-3 (the histogram warps, named barrier 1) take the stages in order:
+// The consumer warps of the split-warp form (int8, zero / constant / threshold, also
+// write-flagged, one group of 8 consumer warps). Warps 0-3 (the histogram warps, named barrier 1) take the stages in order:
 // per window the histogram, the reduce and, on warp 0, the scan and the searches, whose result
 // warp 0 hands over in a slot; they go on to the next window's histogram at once, so warp 0's
 // searches overlap the other histogram warps' work. Warps 4-7 (the replace warps, named barrier 2)
@@ -276,8 +276,8 @@ __device__ bool split_consumers(const Shm &sm, uint8_t *gb, const Layout &L, Sta
             const Win win = make_win(sg, widx, stage0 + s * stage_bytes + sl.k * sg.W, 1);
             const Rep r = load_rep(sl.rep);
             Pow pw = {0u, 0u};
-            uint32_t f = phase_replace<8, RMODE, TR, false, KeysPre, 0, false>(sr, win, r, key, rtid,
-                                                                              &sm.ctl->ncount[par], pw, &sl.rep);
+            uint32_t f = phase_replace<8, RMODE, TR, false, KeysPre, 0, (MODE & kModeFlaggedOnly) != 0>(
+                sr, win, r, key, rtid, &sm.ctl->ncount[par], pw, &sl.rep);
             f = __reduce_add_sync(0xFFFFFFFFu, f);
             if (lane == 0) {
                 if (f) atomicAdd(&sm.ctl->count[par], f);
@@ -457,7 +457,8 @@ persistent_kernel(const Seg *__restrict__ segs, const Tile *__restrict__ tiles, 
         if (!mbar_wait_bounded(inj_bar, 0, kInjectTimeoutNs)) atomicOr(p.status, kStatusTimeout);
     }
     if constexpr (BITS == 8 && G == 1 && (MODE & kModeWarpSplit) != 0) {
-        if (!split_consumers<MODE & 3, CW>(sm, gb, L, meta, stage0, stages, stage_bytes, bar0, p, tid)) {
+        if (!split_consumers<MODE & (3 | kModeFlaggedOnly), CW>(sm, gb, L, meta, stage0, stages, stage_bytes, bar0, p,
+                                                              tid)) {
             atomicOr(p.status, kStatusTimeout);
             atomicExch(&sm.ctl->abort, 1u);
         }

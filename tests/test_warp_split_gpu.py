@@ -5,8 +5,8 @@ window while the other four replace the window before it; the thresholds go from
 other through a ring of hand-over slots. These cases cover what that adds to the joint form:
 the zero, constant and threshold modes, every stage count and tile order, tiles of several
 windows, ragged tails, windows that fill the largest stages, unaligned buffers (the histogram
-warps copy the stage), the CUDA graph, the test hook that delays a CTA, and the plans the form
-does not serve.
+warps copy the stage), the write-flagged in-place form, the CUDA graph, the test hook that
+delays a CTA, and the plans the form does not serve.
 """
 import numpy as np
 import pytest
@@ -87,6 +87,18 @@ def test_injected_timeout_is_reported_and_context_survives(cuda, rfi):
     assert_same(got, oracle_run(xs, [16384] * 2, 8, 3.0, 0), "after injected timeout")
     got, st, _, _ = gpu_run(rfi, xs, [16384] * 2, 8, 3.0, 0, shape=_shape(stages=2))
     assert st == 0
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_write_flagged_in_place(cuda, rfi, mode):
+    """RFI_PLAN_WRITE_FLAGGED in the split-warp form: in place, only the chunks that change are
+    stored, so the buffer ends equal to the oracle's output."""
+    w = workloads.gwb60(nstreams=4)
+    xs = gen_streams(w, GWB_LENS)
+    got, st, _, info = gpu_run(rfi, xs, [16384] * 4, 8, 3.0, mode, 1 if mode == 1 else 0,
+                               flags=rfi.RFI_PLAN_WRITE_FLAGGED, in_place=True, shape=_shape(stages=2))
+    assert st == 0 and info.shape.warp_split == 2
+    assert_same(got, oracle_run(xs, [16384] * 4, 8, 3.0, mode, 1 if mode == 1 else 0), "write-flagged mode %d" % mode)
 
 
 @pytest.mark.parametrize("what", ["noise", "twelve_bit", "four_warps", "two_groups", "pow2_small"])
