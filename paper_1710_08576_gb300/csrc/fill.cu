@@ -5,11 +5,16 @@
 // kernel then overwrites the flagged samples with M + the Philox noise of spread 1.4826·D, keyed
 // by the absolute sample index as always, so the result is the same bits as the one-pass form.
 //
-// Work: every 256 mask words of a window (8192 samples, fewer at a window's end) are a unit;
-// warp g of the grid takes units g, g + nwarps, ... (segment s holds units [fwin[s], fwin[s + 1]),
-// its windows in order, ceil(mask words / 256) units each). A unit of a window whose count is 0
-// is skipped. The unit goes in two halves of 128 words: lane l reads words 4l .. 4l + 3 of a
-// half, and the warp moves their flagged samples into its ring of positions:
+// Work: a unit is a run of 256 mask words; warp g of the grid takes units g, g + nwarps, ...
+// (segment s holds units [fwin[s], fwin[s + 1])), so that at any time the warps read masks and
+// write samples close to one another (giving each warp a run of consecutive units instead
+// made the k = 3 call of the 60-stream benchmark 40 % slower). Windows of at most kFillPackMax
+// samples, a multiple of 128 (fill_packs), are packed: the segment's mask is one array of words
+// (window k's at k * mw, word j covering samples 32j .. 32j + 31 of the segment) cut into units
+// regardless of the windows, so a unit spans several windows and each lane takes M and D of the
+// window its four words belong to. Otherwise every window has ceil(mw / 256) units of its own,
+// and a unit of a window whose count is 0 is skipped. The unit goes in two halves of 128 words: lane l reads words
+// 4l .. 4l + 3 of a half, and the warp moves their flagged samples into its ring of positions:
 //  - a word with at least kFillDense flags goes whole: lane j tests bit j and a ballot with a
 //    prefix popcount gives each flagged lane its place in the ring;
 //  - from the other words every lane gives up one flag per step (its lowest remaining one),
@@ -76,7 +81,9 @@ struct FillRing {
 
 // Segments hold fewer than 2^31 samples (the plan routes longer ones through the one-pass form),
 // so every segment-relative index below fits 32 bits.
-template <int BITS>
+// PACK: some segment of the launch is packed (the instantiation without it is the per-window
+// form alone, with fewer registers).
+template <int BITS, bool PACK>
 __global__ void __launch_bounds__(kFillThreads) noise_fill_kernel(const Seg *__restrict__ segs, int nseg,
                                                                  const uint32_t *__restrict__ fwin, uint32_t nunits,
                                                                  Params p) {
@@ -94,26 +101,43 @@ __global__ void __launch_bounds__(kFillThreads) noise_fill_kernel(const Seg *__r
         }
         const Seg &g = segs[s];
         const uint32_t mw = static_cast<uint32_t>(g.mask_words);
-        const uint32_t upw = (mw + 255u) >> 8;  // units per window
         const uint32_t local = u - fwin[s];
-        const uint32_t k = local / upw;
-        const uint32_t j00 = (local - k * upw) << 8;
-        if (g.counts && g.counts[k] == 0u) continue;
-        const uint32_t md = (static_cast<uint32_t>(g.med[k]) & 0xFFFFu) | (static_cast<uint32_t>(g.mad[k]) << 16);
-        const uint32_t pos0 = k * static_cast<uint32_t>(g.W);
-        const uint32_t *mk = g.mask + static_cast<size_t>(k) * mw;
-        for (uint32_t j0 = j00; j0 < j00 + 256u && j0 < mw; j0 += 128u) {
+        const bool packed = PACK && fill_packs(g.W);
+        const uint32_t *mk = g.mask;
+        uint32_t j00, jend, pos0 = 0u, md = 0u;
+        if (packed) {
+            j00 = local << 8;
+            jend = min(j00 + 256u, static_cast<uint32_t>((g.len + 31) >> 5));  // the words holding samples
+        } else {
+            const uint32_t upw = (mw + 255u) >> 8;  // units per window
+            const uint32_t k = local / upw;
+            j00 = (local - k * upw) << 8;
+            jend = min(j00 + 256u, mw);
+            if (g.counts && g.counts[k] == 0u) continue;
+            md = (static_cast<uint32_t>(g.med[k]) & 0xFFFFu) | (static_cast<uint32_t>(g.mad[k]) << 16);
+            mk += static_cast<size_t>(k) * mw;
+            pos0 = k * static_cast<uint32_t>(g.W);
+        }
+        // a packed segment's words of a lane lie in one window (mw is a multiple of 4)
+        const bool vec = (mw & 3u) == 0u && (reinterpret_cast<uintptr_t>(mk) & 15u) == 0u;
+        const int lg = PACK && (mw & (mw - 1u)) == 0u ? __ffs(mw) - 1 : -1;  // log2 mw, or -1
+        for (uint32_t j0 = j00; j0 < jend; j0 += 128u) {
             const uint32_t jl = j0 + 4u * static_cast<uint32_t>(lane);  // this lane's first word
             uint32_t m[4];
-            if ((mw & 3u) == 0u && (reinterpret_cast<uintptr_t>(mk) & 15u) == 0u) {
-                const uint4 a = jl < mw ? *reinterpret_cast<const uint4 *>(mk + jl) : make_uint4(0u, 0u, 0u, 0u);
+            uint32_t mdl = md;
+            if (vec) {
+                const uint4 a = jl < jend ? *reinterpret_cast<const uint4 *>(mk + jl) : make_uint4(0u, 0u, 0u, 0u);
                 m[0] = a.x;
                 m[1] = a.y;
                 m[2] = a.z;
                 m[3] = a.w;
             } else {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) m[i] = jl + i < mw ? mk[jl + i] : 0u;
+                for (int i = 0; i < 4; ++i) m[i] = jl + i < jend ? mk[jl + i] : 0u;
+            }
+            if (packed && jl < jend) {
+                const uint32_t k = lg >= 0 ? jl >> lg : jl / mw;
+                mdl = (static_cast<uint32_t>(g.med[k]) & 0xFFFFu) | (static_cast<uint32_t>(g.mad[k]) << 16);
             }
             if (!__any_sync(0xFFFFFFFFu, (m[0] | m[1] | m[2] | m[3]) != 0u)) continue;  // on to the next half
             // dense words, one at a time over the whole warp
@@ -127,8 +151,9 @@ __global__ void __launch_bounds__(kFillThreads) noise_fill_kernel(const Seg *__r
                     const int src = __ffs(dense) - 1;
                     dense &= dense - 1u;
                     const uint32_t w = __shfl_sync(0xFFFFFFFFu, wi, src);
+                    const uint32_t mdw = PACK ? __shfl_sync(0xFFFFFFFFu, mdl, src) : mdl;
                     const uint32_t pos = pos0 + 32u * (j0 + 4u * static_cast<uint32_t>(src) + i) + static_cast<uint32_t>(lane);
-                    R.put(((w >> lane) & 1u) != 0u, pos, md);
+                    R.put(((w >> lane) & 1u) != 0u, pos, mdw);
                 }
             }
             // the other words: each lane gives up its lowest remaining flag per step
@@ -142,7 +167,7 @@ __global__ void __launch_bounds__(kFillThreads) noise_fill_kernel(const Seg *__r
                 else if (h1) m[1] = rest;
                 else if (h2) m[2] = rest;
                 else m[3] = rest;
-                R.put(cur != 0u, pos, md);
+                R.put(cur != 0u, pos, mdl);
             }
         }
     }
@@ -151,20 +176,27 @@ __global__ void __launch_bounds__(kFillThreads) noise_fill_kernel(const Seg *__r
 
 }  // namespace dev
 
-int noise_fill_grid(int sm_count) {
+int noise_fill_grid(int sm_count, bool packed) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dev::noise_fill_kernel<8>, dev::kFillThreads, 0) != cudaSuccess || n < 1) {
+    const cudaError_t e = packed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dev::noise_fill_kernel<8, true>, dev::kFillThreads, 0)
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dev::noise_fill_kernel<8, false>, dev::kFillThreads, 0);
+    if (e != cudaSuccess || n < 1) {
         cudaGetLastError();
         n = 1;
     }
     return sm_count * n;
 }
 
-cudaError_t launch_noise_fill(int bits, const Seg *segs, int nseg, const uint32_t *fwin, uint32_t nunits, const Params &p,
-                              int grid, cudaStream_t st) {
+cudaError_t launch_noise_fill(int bits, bool packed, const Seg *segs, int nseg, const uint32_t *fwin, uint32_t nunits,
+                              const Params &p, int grid, cudaStream_t st) {
     if (nunits == 0) return cudaSuccess;
-    if (bits == 8) dev::noise_fill_kernel<8><<<grid, dev::kFillThreads, 0, st>>>(segs, nseg, fwin, nunits, p);
-    else dev::noise_fill_kernel<12><<<grid, dev::kFillThreads, 0, st>>>(segs, nseg, fwin, nunits, p);
+    if (bits == 8) {
+        if (packed) dev::noise_fill_kernel<8, true><<<grid, dev::kFillThreads, 0, st>>>(segs, nseg, fwin, nunits, p);
+        else dev::noise_fill_kernel<8, false><<<grid, dev::kFillThreads, 0, st>>>(segs, nseg, fwin, nunits, p);
+    } else {
+        if (packed) dev::noise_fill_kernel<12, true><<<grid, dev::kFillThreads, 0, st>>>(segs, nseg, fwin, nunits, p);
+        else dev::noise_fill_kernel<12, false><<<grid, dev::kFillThreads, 0, st>>>(segs, nseg, fwin, nunits, p);
+    }
     return cudaGetLastError();
 }
 

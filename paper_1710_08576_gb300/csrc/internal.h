@@ -170,11 +170,15 @@ cudaError_t launch_mom(int bits, const MomChunk *chunks, int nchunks, const int3
 
 // Digital noise as a second pass over segments whose excision pass wrote 0 at the flagged
 // samples, the flag mask, every window's count and every window's M and D (segments of fewer
-// than 2^31 samples). The pass's units are 256 mask words of a window (ceil(ceil(W / 32) / 256)
-// a window); segment s holds units [fwin[s], fwin[s + 1]), nunits = fwin[nseg].
-int noise_fill_grid(int sm_count);
-cudaError_t launch_noise_fill(int bits, const Seg *segs, int nseg, const uint32_t *fwin, uint32_t nunits, const Params &p,
-                              int grid, cudaStream_t st);
+// than 2^31 samples). The pass's units are 256 mask words: of the whole segment's mask when
+// fill_packs(W) (ceil(ceil(len / 32) / 256) units), else of each window (ceil(ceil(W / 32) / 256)
+// a window); segment s holds units [fwin[s], fwin[s + 1]), nunits = fwin[nseg]. packed: some
+// segment of the launch has fill_packs(W).
+constexpr int kFillPackMax = 2048;
+__host__ __device__ inline bool fill_packs(int32_t W) { return W % 128 == 0 && W <= kFillPackMax; }
+int noise_fill_grid(int sm_count, bool packed);
+cudaError_t launch_noise_fill(int bits, bool packed, const Seg *segs, int nseg, const uint32_t *fwin, uint32_t nunits,
+                              const Params &p, int grid, cudaStream_t st);
 
 // Write n (<= kSegBatch) segment descriptors to dst (device) from kernel parameters.
 constexpr int kSegBatch = 32;

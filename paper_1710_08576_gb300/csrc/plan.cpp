@@ -148,15 +148,22 @@ rfi_status plan_alloc_workspace(rfi_plan_s *P) {
     const size_t mc_b = mom ? al(sizeof(MomChunk) * P->mchunks.size()) : 0;
     const size_t pw_b = P->power ? al(2 * sizeof(uint64_t) * P->total_windows) : 0;
     const size_t var_b = al(sizeof(Variant) * P->variants.size());
-    std::vector<uint32_t> fwin;  // the fill pass: unit offsets of the segments (256 mask words a unit)
+    // the fill pass: unit offsets of the segments (256 mask words a unit; for small windows of a
+    // multiple of 128 samples the units run over the words of the whole segment, else over
+    // those of each window)
+    std::vector<uint32_t> fwin;
     if (P->fill) {
         fwin.push_back(0);
+        P->fill_packed = false;
         for (int i = 0; i < P->S; ++i) {
-            const int64_t upw = ((P->W[i] + 31) / 32 + 255) / 256;
-            fwin.push_back(fwin.back() + static_cast<uint32_t>(P->nwin[i] * upw));
+            const bool pk = fill_packs(P->W[i]);
+            const int64_t units = pk ? ((P->len[i] + 31) / 32 + 255) / 256
+                                     : P->nwin[i] * (((P->W[i] + 31) / 32 + 255) / 256);
+            P->fill_packed = P->fill_packed || pk;
+            fwin.push_back(fwin.back() + static_cast<uint32_t>(units));
         }
         P->nfwin = fwin.back();
-        P->fill_grid = noise_fill_grid(P->sm_count);
+        P->fill_grid = noise_fill_grid(P->sm_count, P->fill_packed);
     }
     // one allocation, each array at the next 256-byte boundary
     size_t off = 0;
@@ -232,7 +239,7 @@ rfi_status plan_enqueue_batched(rfi_plan_s *P, cudaStream_t st) {
         const Params p = plan_params(P);
         RFI_CUDA(launch_persistent(P->bits, plan_kernel_mode(P), P->shape, P->grid, P->d_segs, P->d_tiles,
                                    P->ntiles, p, &P->d_ctr->tile_counter, inject, st));
-        if (P->fill) RFI_CUDA(launch_noise_fill(P->bits, P->d_segs, P->S, P->d_fwin, P->nfwin, p, P->fill_grid, st));
+        if (P->fill) RFI_CUDA(launch_noise_fill(P->bits, P->fill_packed, P->d_segs, P->S, P->d_fwin, P->nfwin, p, P->fill_grid, st));
         return RFI_OK;
     }
     // Median of MAD (Eq. 3): M and D of every window, the sliding median of the MADs, then Eq. 1
@@ -247,7 +254,7 @@ rfi_status plan_enqueue_batched(rfi_plan_s *P, cudaStream_t st) {
                                P->d_tiles, P->ntiles, p, &P->d_ctr->tile_counter, 0, st));
     // the apply segments hold each window's M and its MoM: the noise spread of Eq. 3
     if (P->fill)
-        RFI_CUDA(launch_noise_fill(P->bits, P->d_segs + P->S, P->S, P->d_fwin, P->nfwin, p, P->fill_grid, st));
+        RFI_CUDA(launch_noise_fill(P->bits, P->fill_packed, P->d_segs + P->S, P->S, P->d_fwin, P->nfwin, p, P->fill_grid, st));
     return RFI_OK;
 }
 

@@ -66,6 +66,7 @@ struct rfi_plan_s {
     bool fill = false;
     uint32_t *d_fwin = nullptr;
     uint32_t nfwin = 0;
+    bool fill_packed = false;  // some segment's fill units are packed (fill_packs)
     int fill_grid = 0;
     uint32_t *d_fmask = nullptr;  // flag masks of streams called without one (allocated on demand)
     std::vector<int64_t> fmask_off;

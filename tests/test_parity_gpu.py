@@ -134,6 +134,29 @@ def test_misaligned_and_in_place_buffers(cuda, rfi, bits, offset, in_place):
 
 
 @pytest.mark.parametrize("bits", [8, 12])
+@pytest.mark.parametrize("split", [False, True])
+def test_noise_pass_packed_units(cuda, rfi, bits, split):
+    """RFI_PLAN_NOISE_PASS where the second pass packs several windows into one unit of mask
+    words (windows of a multiple of 128 samples up to 2048, powers of two or not) beside windows
+    that keep units of their own, in one launch and split into window classes; ragged, short and
+    one-sample streams."""
+    p = synth.params(seed=33, sigma=16.0 if bits == 8 else 120.0, burst_rate=2e-2, burst_len_max=64, bits=bits)
+    wins = [128, 256, 384, 640, 1024, 1920, 2048, 1000, 4096, 16384, 2048, 128]
+    lens = [37 * 128 + 5, 21 * 256, 9 * 384 + 383, 13 * 640 + 1, 11 * 1024 + 700, 4 * 1920 + 64, 2048 - 7,
+            6 * 1000 + 3, 3 * 4096 + 9, 16384 + 100, 1, 31]
+    xs = [synth.fill(p, s, n) for s, n in enumerate(lens)]
+    flags = rfi.RFI_PLAN_NOISE_PASS | (0 if split else rfi.RFI_PLAN_NO_SPLIT)
+    for k in (2.0, 3.0):
+        got, st, totals, info = gpu_run(rfi, xs, wins, bits, k, 3, seed=5, flags=flags)
+        assert st == 0
+        if not split:
+            assert info.kernels_per_call == 2
+        ref = oracle_run(xs, wins, bits, k, 3, 0, 5)
+        assert_same(got, ref, "bits %d k %g" % (bits, k))
+        assert totals.flagged == sum(int(r["counts"].sum()) for r in ref)
+
+
+@pytest.mark.parametrize("bits", [8, 12])
 def test_noise_pass_without_caller_masks(cuda, rfi, bits):
     """A RFI_PLAN_NOISE_PASS plan called without masks (or counts) flags into the plan's own masks
     for its second pass: the samples equal the oracle's; a later call with masks gives the masks
