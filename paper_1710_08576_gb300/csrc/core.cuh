@@ -968,8 +968,9 @@ __device__ __forceinline__ uint32_t sq4(uint32_t w, uint32_t keep) {
 
 // rsrc: the shared record r was loaded from (its int8 constants are read from there). FO (8-bit
 // in-place form): chunks without a flagged sample are not stored, and in noise mode no chunk is
-// (the noise pass writes every flagged sample).
-template <int BITS, int MODE, int T, bool PW, class K, int OUTF = 0, bool FO = false>
+// (the noise pass writes every flagged sample). PAIR (the split-warp form's replace warps):
+// full rounds go two at a time.
+template <int BITS, int MODE, int T, bool PW, class K, int OUTF = 0, bool FO = false, bool PAIR = false>
 __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, const Rep &r, const K &p,
                                                   int tid, uint32_t *nlc, Pow &pw, const RepShared *rsrc) {
     constexpr int BPS = Geo<BITS>::kBps;
@@ -996,9 +997,7 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
         int base = warp * 32;
         if (r.active && w.vec && mk) {
             // rounds in which all 32 chunks of the warp are full: no bounds checks
-            for (; base + 32 <= nfull; base += T) {
-                const int c = base + lane;
-                uint4 v = d4[c];
+            auto full_round = [&](int c, uint4 v) {
                 if (PW) pw.x += sq4(v.x, ~0u) + sq4(v.y, ~0u) + sq4(v.z, ~0u) + sq4(v.w, ~0u);
                 uint32_t f0, f1, f2, f3;
                 v.x = rep8_word<MODE>(v.x, k, f0);
@@ -1011,7 +1010,20 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
                 mk[c] = static_cast<uint16_t>(bits);
                 flagged += __popc(bits);
                 if (MODE == 3) noise_note8(sm, lane, c, bits, nlc);
+            };
+            // two rounds at a time, both chunks loaded before either is replaced (the loads of the
+            // second overlap the first's arithmetic): zero, constant and threshold in the split-warp
+            // form (1.618 -> 1.607 ms for gwb60's zero call; in the joint form the fp16 output lost
+            // 6 % and the digital copy and the Median-of-MAD apply pass 1 %)
+            if (PAIR && MODE != 3) {
+                for (; base + T + 32 <= nfull; base += 2 * T) {
+                    const uint4 va = d4[base + lane];
+                    const uint4 vb = d4[base + T + lane];
+                    full_round(base + lane, va);
+                    full_round(base + T + lane, vb);
+                }
             }
+            for (; base + 32 <= nfull; base += T) full_round(base + lane, d4[base + lane]);
         }
         // warp-uniform rounds: lane handles chunk base + lane
         for (; base < nchunks; base += T) {

@@ -276,7 +276,7 @@ __device__ bool split_consumers(const Shm &sm, uint8_t *gb, const Layout &L, Sta
             const Win win = make_win(sg, widx, stage0 + s * stage_bytes + sl.k * sg.W, 1);
             const Rep r = load_rep(sl.rep);
             Pow pw = {0u, 0u};
-            uint32_t f = phase_replace<8, RMODE, TR, false, KeysPre, 0, (MODE & kModeFlaggedOnly) != 0>(
+            uint32_t f = phase_replace<8, RMODE, TR, false, KeysPre, 0, (MODE & kModeFlaggedOnly) != 0, true>(
                 sr, win, r, key, rtid, &sm.ctl->ncount[par], pw, &sl.rep);
             f = __reduce_add_sync(0xFFFFFFFFu, f);
             if (lane == 0) {
