@@ -881,7 +881,23 @@ __device__ __forceinline__ void noise_list(const Shm &sm, const Win &w, const Re
                                            uint32_t *nlc, Pow &pw) {
     if (sm.nlist == nullptr) return;
     const uint32_t n = min(*nlc, static_cast<uint32_t>(kNoiseList));
-    for (uint32_t i = static_cast<uint32_t>(tid); i < n; i += T) {
+    uint32_t i = static_cast<uint32_t>(tid);
+    // two entries at a time: the two Philox chains are independent, so their rounds interleave
+    // and fill each other's dependency stalls (twelve60 4.60 -> 4.53 ms per call)
+    for (; i + T < n; i += 2 * T) {
+        const uint32_t pa = sm.nlist[i], pb = sm.nlist[i + T];
+        const int32_t za = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pa, Geo<BITS>::kLo, Geo<BITS>::kHi);
+        const int32_t zb = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pb, Geo<BITS>::kLo, Geo<BITS>::kHi);
+        if (pa != kNoiseSkip) {
+            store_sample<BITS, OUTF>(w.out, pa, za);
+            if (PW) pw.z += static_cast<uint32_t>(za * za);
+        }
+        if (pb != kNoiseSkip) {
+            store_sample<BITS, OUTF>(w.out, pb, zb);
+            if (PW) pw.z += static_cast<uint32_t>(zb * zb);
+        }
+    }
+    for (; i < n; i += T) {
         const uint32_t pos = sm.nlist[i];
         if (pos == kNoiseSkip) continue;
         const int32_t z = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pos, Geo<BITS>::kLo, Geo<BITS>::kHi);
