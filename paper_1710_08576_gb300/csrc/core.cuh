@@ -883,7 +883,8 @@ __device__ __forceinline__ void noise_list(const Shm &sm, const Win &w, const Re
     const uint32_t n = min(*nlc, static_cast<uint32_t>(kNoiseList));
     uint32_t i = static_cast<uint32_t>(tid);
     // two entries at a time: the two Philox chains are independent, so their rounds interleave
-    // and fill each other's dependency stalls (twelve60 4.60 -> 4.53 ms per call)
+    // and fill each other's dependency stalls (60 streams of 2^25 12-bit samples in 8192-sample
+    // windows, a quarter of them flagged: 4.60 -> 4.53 ms per call)
     for (; i + T < n; i += 2 * T) {
         const uint32_t pa = sm.nlist[i], pb = sm.nlist[i + T];
         const int32_t za = noise_value(r.M, r.sigq, p, w.sid, w.abs_idx + pa, Geo<BITS>::kLo, Geo<BITS>::kHi);
@@ -1029,8 +1030,9 @@ __device__ __forceinline__ uint32_t phase_replace(const Shm &sm, const Win &w, c
             };
             // two rounds at a time, both chunks loaded before either is replaced (the loads of the
             // second overlap the first's arithmetic): zero, constant and threshold in the split-warp
-            // form (1.618 -> 1.607 ms for gwb60's zero call; in the joint form the fp16 output lost
-            // 6 % and the digital copy and the Median-of-MAD apply pass 1 %)
+            // form (1.618 -> 1.607 ms for a zero-mode call over 60 streams of 2^26 int8 samples in
+            // 16384-sample windows; in the joint form the fp16 output lost 6 % and the digital copy
+            // and the Median-of-MAD apply pass 1 %)
             if (PAIR && MODE != 3) {
                 for (; base + T + 32 <= nfull; base += 2 * T) {
                     const uint4 va = d4[base + lane];
